@@ -1,0 +1,337 @@
+#!/usr/bin/env python3
+"""Throughput of the shearlet transform hot path on GB300.
+
+One step = shearlet decomposition + reconstruction (fwd + inv) of a batch of
+B = 16 images of 512 x 512 with the K = 49 filters of 4 scales (shear levels
+1, 1, 2, 2), float32 coefficients.  Metric: shearlet coefficients per second,
+B K N^2 / t(step).  Inputs are seeded synthetic cartoons (the paper's images
+are not available).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank processes its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+``--impl reference`` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_IMG, K_FILT, B_IMG, SCALES = 512, 49, 16, 4
+METRIC = "Shearlet coeffs/s fwd+inv at 512^2, 49 filters"
+UNIT = "coeffs/s"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def _config(extra=None):
+    cfg = {"workload": "decompose+reconstruct, B=16 x 512x512 float32 images, K=49 "
+                       "(4 scales, shear levels 1,1,2,2), float32 coefficients",
+           "rows": N_IMG, "cols": N_IMG, "filters": K_FILT, "global_batch": B_IMG,
+           "coeff_dtype": "f32", "l2": "flushed between timed steps (512 MiB write); "
+                                        "coefficients (822 MB) also exceed L2"}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+def _algorithmic_bytes(B, K, N, M, s=4):
+    """Step bytes: dec reads images + filters, writes coefficients; rec reads
+    coefficients + filters + 1/W, writes images (half-spectrum float32 filters)."""
+    H = N * (M // 2 + 1)
+    dec = B * (4 * N * M + s * K * N * M) + 4 * K * H
+    rec = B * (s * K * N * M + 4 * N * M) + 4 * K * H + 4 * H
+    return dec, rec
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    def __init__(self, device_index=0):
+        self.samples = []
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.samples.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        mx = [float(s[2]) for s in self.samples if s[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for s in self.samples for k in range(4)
+                          if s[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------------- CPU
+_ORACLE_BANK = []
+
+
+def _oracle_sample(seconds_target=12.0, max_images=B_IMG):
+    """Oracle dec+rec on whole images of the workload until ~seconds_target."""
+    import numpy as np
+    from oracle import bank as Bk
+    from oracle import transform as OT
+    from paper_2006_04591_gb300 import synth
+    if not _ORACLE_BANK:
+        _ORACLE_BANK.append(Bk.shearlet_bank(N_IMG, N_IMG, SCALES))
+    ref = _ORACLE_BANK[0]
+    done, t0 = 0, time.perf_counter()
+    while done < max_images:
+        x = synth.cartoon(N_IMG, N_IMG, 100 + done).astype(np.float32)
+        c = OT.decompose(x, ref["psi_hat"]).real
+        OT.reconstruct(c, ref["psi_hat"])
+        done += 1
+        if time.perf_counter() - t0 >= seconds_target:
+            break
+    dt = time.perf_counter() - t0
+    return done, dt
+
+
+def _cpu_cores_used():
+    # numpy.fft (pocketfft) runs on one thread; the oracle loops in Python.
+    return 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    per_step = []
+    imgs = 0
+    for s in range(args.warmup + args.steps):
+        n, dt = _oracle_sample(seconds_target=4.0, max_images=1)
+        if s >= args.warmup:
+            per_step.append(dt / n)
+            imgs += n
+    t_img = statistics.mean(per_step)
+    value = K_FILT * N_IMG * N_IMG / t_img
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_img * B_IMG * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config({"sample": "1 image (of 16) per step, dec+rec, K=49; "
+                                     "ms_per_step scaled to the 16-image batch"}),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores_used(),
+                         "kind": "oracle", "sample": "%d images x K=49 dec+rec at 512^2" % imgs},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------- GPU
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2006_04591_gb300 import shearlet as S
+    from paper_2006_04591_gb300 import synth
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2006_04591_gb300 import _build
+    _build.build()
+    bank = S.Bank.create(N_IMG, N_IMG, SCALES, device=local)
+    assert bank.K == K_FILT
+    B, N, K = B_IMG, N_IMG, K_FILT
+    x_host = np.stack([synth.cartoon(N, N, 100 + rank * B + b) for b in range(B)]).astype(np.float32)
+    x = torch.from_numpy(x_host).to(dev)
+    coeffs = torch.empty((B, K, N, N), dtype=torch.float32, device=dev)
+    xr = torch.empty((B, N, N), dtype=torch.float32, device=dev)
+    ws_d = bank.workspace(S.SHL_OP_DECOMPOSE, B)
+    ws_r = bank.workspace(S.SHL_OP_RECONSTRUCT, B)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        bank.decompose(x, out=coeffs, ws=ws_d)
+        bank.reconstruct(coeffs, out=xr, ws=ws_r)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    err = ((xr - x).abs().max() / x.abs().max()).item()
+
+    def timed(fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for i in range(steps):
+            flush.fill_(float(i))
+            evs[i][0].record(stream)
+            fn()
+            evs[i][1].record(stream)
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in evs]
+
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    n0 = S.shl_launch_count()
+    times = timed(step, args.steps)
+    launches = S.shl_launch_count() - n0
+    clock_info = clocks.stop()
+    t_step = sum(times) / len(times) / 1e3
+    if world > 1:
+        t = torch.tensor([t_step], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_step = t.item()
+        dist.barrier()
+
+    # per-kernel timing with CUDA events on the launch stream (separate pass)
+    S.shl_profile_enable(1)
+    S.shl_profile_read()
+    prof_times = timed(step, args.steps)
+    S.shl_profile_enable(0)
+    prof = S.shl_profile_read()
+    t_prof = sum(prof_times) / len(prof_times) / 1e3
+
+    # end to end through the public API with pinned host buffers
+    xh = torch.from_numpy(x_host).pin_memory()
+    outh = torch.empty((B, N, N), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        xd = xh.to(dev, non_blocking=True)
+        bank.decompose(xd, out=coeffs, ws=ws_d)
+        bank.reconstruct(coeffs, out=xr, ws=ws_r)
+        outh.copy_(xr, non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e2e_times = timed(e2e_step, args.steps)
+    t_e2e = sum(e2e_times) / len(e2e_times) / 1e3
+
+    coeffs_per_step = B * K * N * N * world
+    value = coeffs_per_step / t_step
+    dec_b, rec_b = _algorithmic_bytes(B, K, N, N)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # dominant kernel and its algorithmic bytes per launch
+    kern = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
+    roof = None
+    if kern[0] is not None:
+        name, rec = kern
+        per_launch_ms = rec["ms"] / rec["launches"]
+        per_step_launches = rec["launches"] / args.steps
+        per_kernel_bytes = {
+            "rows_c2r_coeffs": B * K * N * N * 4,     # coefficient stores of dec
+            "rows_r2c_coeffs": B * K * N * N * 4,     # coefficient loads of rec
+            "rows_r2c_image": B * N * N * 4,
+            "rows_c2r_image": B * N * N * 4,
+        }
+        step_bytes = per_kernel_bytes.get(name, 0)
+        alg = step_bytes / per_step_launches if per_step_launches else 0
+        achieved = alg / (per_launch_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "peak_source": peak_src, "launch_ms": per_launch_ms,
+                "algorithmic_bytes_per_launch": alg}
+
+    step_alg = dec_b + rec_b
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": _config({"parallelism": "replicas" if world > 1 else "single"}),
+        "step_hbm": {"algorithmic_bytes": step_alg,
+                     "achieved_gbs": step_alg / t_step / 1e9,
+                     "frac_of_peak": step_alg / t_step / 1e9 / hbm_peak,
+                     "peak": hbm_peak, "peak_source": peak_src},
+        "roofline": roof,
+        "kernels": {k: {"launches_per_step": v["launches"] / args.steps,
+                        "ms_per_step": v["ms"] / args.steps} for k, v in prof.items()},
+        "profiled_ms_per_step": t_prof * 1e3,
+        "e2e": {"value": coeffs_per_step / t_e2e, "unit": UNIT,
+                "h2d_bytes_per_step": B * N * N * 4, "d2h_bytes_per_step": B * N * N * 4},
+        "gpu_launches": launches,
+        "clocks": clock_info,
+        "pr_rel_err": err,
+    }
+    if rank == 0:
+        if not args.no_cpu_baseline and world == 1:
+            n, dt = _oracle_sample(seconds_target=args.cpu_seconds)
+            cpu_val = n * K * N * N / dt
+            line["cpu_baseline"] = {"value": cpu_val, "unit": UNIT, "cores": _cpu_cores_used(),
+                                    "kind": "oracle",
+                                    "sample": "%d of the 16 images, dec+rec K=49 at 512^2, "
+                                              "FP64 numpy oracle, %.1f s" % (n, dt)}
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,225 @@
+/*
+ * shearlet.h - C ABI of libshearlet, the GB300 (sm_103a) digital shearlet
+ * transform after tfShearlab (arXiv 2006.04591).
+ *
+ * The library exposes the paper's three operations (Sec. 3.4): build the
+ * filter bank (``getshearletsystem2D``), decompose (``tfsheardec2D``) and
+ * reconstruct (``tfshearrec2D``), plus the adjoint of each transform.  All
+ * transform work runs in hand-written CUDA kernels; nothing here falls back to
+ * the CPU.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Return value: shl_status.  SHL_OK (0) on success; otherwise nothing was
+ * launched, or (for SHL_ECUDA) the launch failed, and shl_last_error_detail()
+ * gives a thread-local message.  No call aborts, traps or throws.  Kernel
+ * faults are asynchronous and surface at the next CUDA call or at
+ * shl_sync().
+ *
+ * Streams: ``stream`` is a cudaStream_t passed as void* (NULL = legacy
+ * default stream).  Every launch goes on that stream; no call synchronises.
+ *
+ * Images: ``rows`` x ``cols`` real float32, row-major, batch-major:
+ * x[b][y][x].  rows and cols are powers of two in [16, 2048].
+ *
+ * Coefficients: c[b][i][y][x] (batch, filter, row, column), float32 or
+ * bfloat16 (round-to-nearest-even on store).  This is the paper's
+ * [1, N, M, nShearlets] tensor with the filter axis moved before the image
+ * axes (paper coeffs[0, y, x, i] == c[0][i][y][x]), so each subband is one
+ * contiguous image.
+ *
+ * Filters: K real, even spectra G_i in natural DFT order (index 0 = zero
+ * frequency), i.e. ifftshift of the paper's centred ``shearletFilters[i]``.
+ * The library keeps the half-spectrum columns 0..cols/2 on the device.
+ *
+ * Ownership: the library owns a bank (device spectra, 1/W, RMS, indices).
+ * The caller owns all image, coefficient, threshold and workspace buffers,
+ * which must be device pointers on the bank's device, 16-byte aligned, and
+ * must not alias each other.  The hot calls allocate nothing.
+ *
+ * Concurrency: a bank is immutable after creation; calls with distinct
+ * workspaces may run concurrently on different streams.
+ */
+#ifndef SHEARLET_H
+#define SHEARLET_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SHL_ABI_VERSION 1
+
+typedef enum {
+  SHL_OK = 0,
+  SHL_EINVAL = 1,        /* bad argument (null pointer, size, alignment)   */
+  SHL_ENOMEM = 2,        /* device or host allocation failed (bank create) */
+  SHL_ECUDA = 3,         /* a CUDA runtime call or launch failed           */
+  SHL_EUNSUPPORTED = 4,  /* size or option this build does not support     */
+  SHL_ETIMEOUT = 5,      /* a bounded device wait gave up                  */
+  SHL_EDEVICE = 6        /* a kernel reported an error through its flag    */
+} shl_status;
+
+typedef enum { SHL_F32 = 0, SHL_BF16 = 1 } shl_dtype;
+
+/* shl_decompose flags */
+#define SHL_DUAL_WEIGHTED 1  /* multiply by G_i / W: adjoint of reconstruct */
+
+/* shl_workspace_size ops */
+typedef enum {
+  SHL_OP_DECOMPOSE = 0,
+  SHL_OP_RECONSTRUCT = 1, /* also shl_adjoint */
+} shl_op;
+
+typedef struct shl_bank shl_bank;
+
+int shl_abi_version(void);
+const char* shl_status_str(shl_status s);
+/* Thread-local text for the last non-OK status returned on this thread. */
+const char* shl_last_error_detail(void);
+
+/*
+ * shl_bank_create - build the digital shearlet system (Sec. 2.1, Sec. 3.4
+ * ``getshearletsystem2D(rows, cols, nScales, ...)``) in float64 on the host
+ * and upload it to ``device``.
+ *   n_scales      J >= 1.
+ *   shear_levels  J ints (scale 0 = coarsest) or NULL for ceil((j+1)/2).
+ *                 Levels must be in [0, 4].
+ *   full          0: cone 2 omits the two diagonal shears +-2^l (17/33/49
+ *                 filters for 2/3/4 scales, Eq. 3.2); 1: keeps them.
+ *   out           receives the bank; release with shl_bank_destroy.
+ * Filters: 1D maximally flat low-pass h (9 taps, 3 dB at pi/2) and its
+ * mirror g, iterated filters h_j / g_j, McClellan fan filter P, digital
+ * shear of Eqs. 2.4-2.5.  Order: 0 = low-pass, then per scale (coarse to
+ * fine) cone 1 with shear k ascending, then cone 2 with k ascending.
+ * device < 0 builds a host-only bank: shl_bank_query / shl_bank_copy_info
+ * work (no GPU needed), transform calls return SHL_EINVAL.
+ * Errors: SHL_EINVAL for bad sizes / levels, SHL_ENOMEM, SHL_ECUDA.
+ */
+shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_levels,
+                           int full, int device, shl_bank** out);
+
+/*
+ * shl_bank_create_from_spectra - use caller-supplied spectra (Sec. 3.4: any
+ * filter tensor ``tfshearlets`` of shape [1, N, M, K]).
+ *   spectra  host float64 [K][rows][cols], natural order, real.  Each must
+ *            be even, G(-k) == G(k), to 1e-9 of its max |G|, and the dual
+ *            weights W = sum_i G_i^2 must be > 0 everywhere, else SHL_EINVAL.
+ *   idx      host int [K][3] (cone, scale, shear) copied for reference, or
+ *            NULL (all zeros).
+ * RMS_i = sqrt(sum G_i^2 / (rows cols)) is computed in float64.
+ * device < 0 builds a host-only bank as for shl_bank_create.
+ */
+shl_status shl_bank_create_from_spectra(int rows, int cols, int K, const double* spectra,
+                                        const int* idx, int device, shl_bank** out);
+
+shl_status shl_bank_destroy(shl_bank* bank);
+
+/* Number of filters and image size of a bank. Any out pointer may be NULL. */
+shl_status shl_bank_query(const shl_bank* bank, int* K, int* rows, int* cols);
+
+/*
+ * shl_bank_copy_info - copy host-side float64 data of a bank (Sec. 3.4: the
+ * system's filters, its RMS array and its index array; and the dual frame
+ * weights ``tfdualFrameWeights``).  Any out pointer may be NULL.
+ *   idx [K][3], rms [K], spectra [K][rows][cols] natural order,
+ *   dual_w [rows][cols] natural order (W = sum_i G_i^2).
+ */
+shl_status shl_bank_copy_info(const shl_bank* bank, int* idx, double* rms, double* spectra,
+                              double* dual_w);
+
+/*
+ * shl_workspace_size - bytes of device workspace ``op`` needs for ``batch``
+ * images.  The workspace holds the image spectra (decompose) or the
+ * per-image accumulators (reconstruct / adjoint) plus an L2-sized staging
+ * area for per-subband intermediates.  Its contents on entry are ignored.
+ */
+shl_status shl_workspace_size(const shl_bank* bank, shl_op op, int batch, size_t* bytes);
+
+/*
+ * shl_decompose - shearlet decomposition (Sec. 3.4, Alg. "Shearlet
+ * Decomposition" and the ``tfsheardec2D`` listing):
+ *   c[b][i] = IFFT2( G_i * FFT2(x[b]) )         flags = 0
+ *   c[b][i] = IFFT2( G_i / W * FFT2(x[b]) )     flags = SHL_DUAL_WEIGHTED
+ * (the second is the adjoint of shl_reconstruct).  IFFT2 includes 1/(rows
+ * cols).  The Fourier shifts of the paper cancel for even sizes and are not
+ * performed.  Coefficients are real.
+ *   x       device float32 [batch][rows][cols].
+ *   coeffs  device [batch][K][rows][cols] of dtype (SHL_F32 / SHL_BF16).
+ *   ws      device workspace of >= shl_workspace_size(DECOMPOSE) bytes.
+ * batch == 0 is a no-op.
+ */
+shl_status shl_decompose(const shl_bank* bank, const float* x, int batch, void* coeffs,
+                         shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream);
+
+/*
+ * shl_decompose_masked - decomposition of u = mask * (f_masked - f_est) +
+ * f_est, the input of one step of the inpainting iteration (Sec. 4.3, Alg.
+ * "Shearlet inpainting by iterative hard thresholding"), with u formed while
+ * the images are loaded.
+ *   f_masked, f_est  device float32 [batch][rows][cols];
+ *   mask             device uint8 [batch][rows][cols], nonzero = observed.
+ * Other arguments as shl_decompose (flags must be 0).
+ */
+shl_status shl_decompose_masked(const shl_bank* bank, const float* f_masked,
+                                const unsigned char* mask, const float* f_est, int batch,
+                                void* coeffs, shl_dtype dtype, void* ws, size_t ws_bytes,
+                                void* stream);
+
+/*
+ * shl_reconstruct - shearlet reconstruction (Sec. 3.4, Alg. "Shearlet
+ * reconstruction" and the ``tfshearrec2D`` listing; Eq. 2.7):
+ *   x[b] = IFFT2( (1/W) * sum_{i=0..K-1} G_i * FFT2(T(c[b][i])) )
+ * summed in the fixed order i = 0..K-1 in float32.  T is the hard
+ * threshold of Sec. 4.2 applied while the coefficients are read: an entry
+ * with |c| < thresh[b][i] becomes 0 (ties are kept).
+ *   coeffs  device [batch][K][rows][cols] of dtype.
+ *   thresh  device float32 [batch][K], or NULL for no thresholding.
+ *   x_out   device float32 [batch][rows][cols].
+ *   ws      device workspace of >= shl_workspace_size(RECONSTRUCT) bytes.
+ */
+shl_status shl_reconstruct(const shl_bank* bank, const void* coeffs, shl_dtype dtype, int batch,
+                           const float* thresh, float* x_out, void* ws, size_t ws_bytes,
+                           void* stream);
+
+/*
+ * shl_adjoint - adjoint of shl_decompose: shl_reconstruct without 1/W,
+ *   x[b] = IFFT2( sum_i G_i * FFT2(T(c[b][i])) ).
+ * Arguments as shl_reconstruct.
+ */
+shl_status shl_adjoint(const shl_bank* bank, const void* coeffs, shl_dtype dtype, int batch,
+                       const float* thresh, float* x_out, void* ws, size_t ws_bytes,
+                       void* stream);
+
+/*
+ * shl_subband_absmax - out[b][i] = max_{y,x} |c[b][i][y][x]| / scale_i with
+ * scale_i = RMS_i when by_rms != 0, else 1.  Used for the inpainting
+ * threshold start value delta_init = max_{i,n} |c_i(n)| / RMS_i (Sec. 4.3).
+ *   out  device float32 [batch][K].
+ */
+shl_status shl_subband_absmax(const shl_bank* bank, const void* coeffs, shl_dtype dtype,
+                              int batch, int by_rms, float* out, void* stream);
+
+/*
+ * Launch accounting (no counterpart in the paper; instrumentation for
+ * measurement).  shl_launch_count returns the number of kernels this
+ * process's library calls have launched.  While shl_profile_enable(1) is in
+ * effect every launch is bracketed by CUDA events recorded on its stream;
+ * shl_profile_read waits for them and writes a JSON object
+ * {"kernel": {"launches": n, "ms": total}, ...} into buf (len bytes) and
+ * clears the records.  SHL_EINVAL if buf is too small (output truncated).
+ */
+long long shl_launch_count(void);
+shl_status shl_profile_enable(int on);
+shl_status shl_profile_read(char* buf, size_t len);
+
+/* Wait for all work on ``stream``; returns SHL_ECUDA with the CUDA error text
+ * if a kernel faulted. */
+shl_status shl_sync(void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SHEARLET_H */

@@ -1,0 +1,486 @@
+// api.cpp - the C ABI declared in include/shearlet.h.
+//
+// Validation, bank ownership and the launch sequences of the transform live
+// here; all arithmetic on images and coefficients runs in the kernels of
+// rows.cu and cols.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <cstdint>
+#include <cstdlib>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/shearlet.h"
+#include "internal.h"
+
+struct shl_bank {
+  int device = 0, N = 0, M = 0, Mh = 0, K = 0;
+  std::vector<double> spectra;   // [K][N][M]
+  std::vector<int> idx;          // [K][3]
+  std::vector<double> rms;       // [K]
+  std::vector<double> dual_w;    // [N][M]
+  float* dG = nullptr;           // [K][N][Mh] half spectra
+  float* dInvW = nullptr;        // [N][Mh]
+  float2* dTw = nullptr;         // [TW_P]
+  float* dRms = nullptr;         // [K]
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+shl_status fail(shl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+shl_status cuda_fail(cudaError_t e, const char* where) {
+  return fail(SHL_ECUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+struct DevGuard {
+  int prev = -1;
+  explicit DevGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DevGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// ------------------------------------------------------- launch accounting
+std::atomic<long long> g_launches{0};
+std::atomic<int> g_profile{0};
+struct ProfRec { const char* name; cudaEvent_t a, b; };
+std::mutex g_prof_mu;
+std::vector<ProfRec> g_prof;
+
+// Brackets one library launch: counts it and, when profiling is on, records
+// CUDA events before and after it on the launch stream.
+struct Launch {
+  const char* name;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr, b = nullptr;
+  Launch(const char* n, cudaStream_t s) : name(n), st(s) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (g_profile.load(std::memory_order_relaxed)) {
+      if (cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+        cudaEventRecord(a, st);
+    }
+  }
+  ~Launch() {
+    if (a && b) {
+      cudaEventRecord(b, st);
+      std::lock_guard<std::mutex> lk(g_prof_mu);
+      g_prof.push_back({name, a, b});
+    }
+  }
+};
+
+// Subbands per chunk: the per-subband staging area is sized to stay in L2.
+int stage_subbands(const shl_bank* b) {
+  static const double mb = [] {
+    const char* e = std::getenv("SHL_STAGE_MB");
+    double v = e ? std::atof(e) : 32.0;
+    return v > 0 ? v : 32.0;
+  }();
+  const double per = double(b->N) * b->Mh * sizeof(float2);
+  int s = (int)(mb * 1024.0 * 1024.0 / per);
+  return s < 1 ? 1 : s;
+}
+
+size_t plane_bytes(const shl_bank* b) { return (size_t)b->N * b->Mh * sizeof(float2); }
+
+size_t ws_need(const shl_bank* b, int batch) {
+  const long long sub = (long long)batch * b->K;
+  const long long S = std::min<long long>(stage_subbands(b), sub);
+  return align256((size_t)batch * plane_bytes(b)) + align256((size_t)S * plane_bytes(b));
+}
+
+void free_bank(shl_bank* b) {
+  if (!b) return;
+  if (b->dG) cudaFree(b->dG);
+  if (b->dInvW) cudaFree(b->dInvW);
+  if (b->dTw) cudaFree(b->dTw);
+  if (b->dRms) cudaFree(b->dRms);
+  delete b;
+}
+
+shl_status upload_bank(shl_bank* b) {
+  const int N = b->N, M = b->M, Mh = b->Mh, K = b->K;
+  const bool host_only = b->device < 0;
+  b->dual_w.assign((size_t)N * M, 0.0);
+  b->rms.assign(K, 0.0);
+  for (int i = 0; i < K; ++i) {
+    const double* G = b->spectra.data() + (size_t)i * N * M;
+    double s = 0.0;
+    for (size_t e = 0; e < (size_t)N * M; ++e) {
+      b->dual_w[e] += G[e] * G[e];
+      s += G[e] * G[e];
+    }
+    b->rms[i] = std::sqrt(s / (double(N) * M));
+  }
+  for (size_t e = 0; e < (size_t)N * M; ++e)
+    if (!(b->dual_w[e] > 0.0)) return fail(SHL_EINVAL, "dual frame weights W = sum G_i^2 must be > 0");
+  if (host_only) return SHL_OK;
+  std::vector<float> hG((size_t)K * N * Mh), hW((size_t)N * Mh), hR(K);
+  for (int i = 0; i < K; ++i)
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < Mh; ++x)
+        hG[((size_t)i * N + y) * Mh + x] = (float)b->spectra[((size_t)i * N + y) * M + x];
+  for (int y = 0; y < N; ++y)
+    for (int x = 0; x < Mh; ++x) hW[(size_t)y * Mh + x] = (float)(1.0 / b->dual_w[(size_t)y * M + x]);
+  for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
+  std::vector<float2> hT(shl::TW_P);
+  const double PI = 3.14159265358979323846264338327950288;
+  for (int q = 0; q < shl::TW_P; ++q) {
+    const double a = -2.0 * PI * q / shl::TW_P;
+    hT[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  DevGuard g(b->device);
+  if (cudaMalloc(&b->dG, hG.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->dInvW, hW.size() * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->dTw, hT.size() * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&b->dRms, hR.size() * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SHL_ENOMEM, "cudaMalloc failed for the filter bank");
+  }
+  cudaError_t e;
+  if ((e = cudaMemcpy(b->dG, hG.data(), hG.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dInvW, hW.data(), hW.size() * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dTw, hT.data(), hT.size() * sizeof(float2), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dRms, hR.data(), hR.size() * sizeof(float), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "bank upload");
+  return SHL_OK;
+}
+
+shl_status check_size(int rows, int cols) {
+  if (!pow2_in(rows, 16, 2048) || !pow2_in(cols, 16, 2048))
+    return fail(SHL_EUNSUPPORTED, "rows and cols must be powers of two in [16, 2048]");
+  return SHL_OK;
+}
+
+shl_status check_common(const shl_bank* b, int batch, const void* ws, size_t ws_bytes,
+                        shl_op op) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  if (b->device < 0) return fail(SHL_EINVAL, "bank was created host-only (device < 0)");
+  if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
+  if (batch == 0) return SHL_OK;
+  if (!ws || !aligned16(ws)) return fail(SHL_EINVAL, "workspace must be a 16-byte aligned device pointer");
+  (void)op;
+  if (ws_bytes < ws_need(b, batch))
+    return fail(SHL_EINVAL, "workspace too small (see shl_workspace_size)");
+  return SHL_OK;
+}
+
+shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
+                          const unsigned char* mask, const float* fest, int batch, void* coeffs,
+                          shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream) {
+  shl_status s = check_common(b, batch, ws, ws_bytes, SHL_OP_DECOMPOSE);
+  if (s != SHL_OK || batch == 0) return s;
+  if (!x || !coeffs || !aligned16(x) || !aligned16(coeffs))
+    return fail(SHL_EINVAL, "x and coeffs must be 16-byte aligned device pointers");
+  if (mode == shl::IN_MASKED && (!mask || !fest || !aligned16(fest) || !aligned16(mask)))
+    return fail(SHL_EINVAL, "mask and f_est must be 16-byte aligned device pointers");
+  if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
+  if (flags & ~SHL_DUAL_WEIGHTED) return fail(SHL_EINVAL, "unknown flags");
+  DevGuard g(b->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int N = b->N, M = b->M, K = b->K;
+  float2* X = static_cast<float2*>(ws);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                        align256((size_t)batch * plane_bytes(b)));
+  cudaError_t e;
+  shl::RowR2CArgs ra{};
+  ra.in = x; ra.mask = mask; ra.fest = fest; ra.out = X; ra.thresh = nullptr;
+  ra.tw = b->dTw; ra.nlines = batch * N; ra.N = N;
+  { Launch L_("rows_r2c_image", st); e = shl::launch_rows_r2c(M, mode, false, ra, st); }
+  if (e) return cuda_fail(e, "rows_r2c");
+  shl::ColArgs ca{};
+  ca.data = X; ca.Mh = b->Mh; ca.tw = b->dTw; ca.K = K;
+  { Launch L_("cols_fwd", st); e = shl::launch_cols(N, shl::COL_FWD, ca, batch, st); }
+  if (e) return cuda_fail(e, "cols_fwd");
+  const int total = batch * K, S = stage_subbands(b);
+  const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  for (int s0 = 0; s0 < total; s0 += S) {
+    const int Sc = std::min(S, total - s0);
+    shl::ColArgs d{};
+    d.data = X; d.out = Z; d.G = b->dG; d.invW = (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr;
+    d.tw = b->dTw; d.scale = (float)(1.0 / (double(N) * M)); d.Mh = b->Mh; d.K = K;
+    d.s0 = s0; d.S = Sc;
+    { Launch L_("cols_dec_inv", st); e = shl::launch_cols(N, shl::COL_DEC_INV, d, Sc, st); }
+    if (e) return cuda_fail(e, "cols_dec_inv");
+    shl::RowC2RArgs c{};
+    c.in = Z; c.out = static_cast<char*>(coeffs) + (size_t)s0 * N * M * esz;
+    c.tw = b->dTw; c.nlines = Sc * N;
+    { Launch L_("rows_c2r_coeffs", st); e = shl::launch_rows_c2r(M, dtype == SHL_BF16, c, st); }
+    if (e) return cuda_fail(e, "rows_c2r");
+  }
+  return SHL_OK;
+}
+
+shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                            const float* thresh, float* x_out, void* ws, size_t ws_bytes,
+                            void* stream, bool weights) {
+  shl_status s = check_common(b, batch, ws, ws_bytes, SHL_OP_RECONSTRUCT);
+  if (s != SHL_OK || batch == 0) return s;
+  if (!coeffs || !x_out || !aligned16(coeffs) || !aligned16(x_out))
+    return fail(SHL_EINVAL, "coeffs and x_out must be 16-byte aligned device pointers");
+  if (thresh && (reinterpret_cast<uintptr_t>(thresh) & 3u))
+    return fail(SHL_EINVAL, "thresh must be 4-byte aligned");
+  if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
+  DevGuard g(b->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int N = b->N, M = b->M, K = b->K;
+  float2* A = static_cast<float2*>(ws);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                        align256((size_t)batch * plane_bytes(b)));
+  const int total = batch * K, S = stage_subbands(b);
+  const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  cudaError_t e;
+  for (int s0 = 0; s0 < total; s0 += S) {
+    const int Sc = std::min(S, total - s0);
+    shl::RowR2CArgs ra{};
+    ra.in = static_cast<const char*>(coeffs) + (size_t)s0 * N * M * esz;
+    ra.out = Z; ra.thresh = thresh ? thresh + s0 : nullptr; ra.tw = b->dTw;
+    ra.nlines = Sc * N; ra.N = N;
+    {
+      Launch L_("rows_r2c_coeffs", st);
+      e = shl::launch_rows_r2c(M, dtype == SHL_BF16 ? shl::IN_BF16 : shl::IN_F32,
+                               thresh != nullptr, ra, st);
+    }
+    if (e) return cuda_fail(e, "rows_r2c");
+    shl::ColArgs ca{};
+    ca.in = Z; ca.acc = A; ca.G = b->dG; ca.tw = b->dTw; ca.Mh = b->Mh; ca.K = K;
+    ca.s0 = s0; ca.S = Sc; ca.b_lo = s0 / K;
+    const int b_hi = (s0 + Sc - 1) / K;
+    { Launch L_("cols_rec_acc", st); e = shl::launch_cols(N, shl::COL_REC_ACC, ca, b_hi - ca.b_lo + 1, st); }
+    if (e) return cuda_fail(e, "cols_rec_acc");
+  }
+  shl::ColArgs f{};
+  f.data = A; f.invW = weights ? b->dInvW : nullptr; f.tw = b->dTw;
+  f.scale = (float)(1.0 / (double(N) * M)); f.Mh = b->Mh; f.K = K;
+  { Launch L_("cols_final_inv", st); e = shl::launch_cols(N, shl::COL_FINAL_INV, f, batch, st); }
+  if (e) return cuda_fail(e, "cols_final");
+  shl::RowC2RArgs c{};
+  c.in = A; c.out = x_out; c.tw = b->dTw; c.nlines = batch * N;
+  { Launch L_("rows_c2r_image", st); e = shl::launch_rows_c2r(M, false, c, st); }
+  if (e) return cuda_fail(e, "rows_c2r");
+  return SHL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int shl_abi_version(void) { return SHL_ABI_VERSION; }
+
+const char* shl_status_str(shl_status s) {
+  switch (s) {
+    case SHL_OK: return "ok";
+    case SHL_EINVAL: return "invalid argument";
+    case SHL_ENOMEM: return "out of memory";
+    case SHL_ECUDA: return "CUDA error";
+    case SHL_EUNSUPPORTED: return "unsupported";
+    case SHL_ETIMEOUT: return "device wait timed out";
+    case SHL_EDEVICE: return "device reported an error";
+  }
+  return "unknown status";
+}
+
+const char* shl_last_error_detail(void) { return g_err.c_str(); }
+
+shl_status shl_bank_create_from_spectra(int rows, int cols, int K, const double* spectra,
+                                        const int* idx, int device, shl_bank** out) {
+  if (!out) return fail(SHL_EINVAL, "out is NULL");
+  *out = nullptr;
+  shl_status s = check_size(rows, cols);
+  if (s != SHL_OK) return s;
+  if (K < 1 || K > 4096 || !spectra) return fail(SHL_EINVAL, "need 1 <= K <= 4096 and spectra");
+  const int N = rows, M = cols;
+  for (int i = 0; i < K; ++i) {
+    const double* G = spectra + (size_t)i * N * M;
+    double mx = 0.0, asym = 0.0;
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < M; ++x) {
+        const double a = G[(size_t)y * M + x], bb = G[(size_t)((N - y) % N) * M + (M - x) % M];
+        if (!std::isfinite(a)) return fail(SHL_EINVAL, "spectra must be finite");
+        mx = std::max(mx, std::fabs(a));
+        asym = std::max(asym, std::fabs(a - bb));
+      }
+    if (asym > 1e-9 * mx)
+      return fail(SHL_EINVAL, "spectrum " + std::to_string(i) + " is not even: G(-k) != G(k)");
+  }
+  shl_bank* b = new shl_bank();
+  b->device = device; b->N = N; b->M = M; b->Mh = M / 2 + 1; b->K = K;
+  b->spectra.assign(spectra, spectra + (size_t)K * N * M);
+  b->idx.assign((size_t)K * 3, 0);
+  if (idx) std::memcpy(b->idx.data(), idx, sizeof(int) * 3 * K);
+  s = upload_bank(b);
+  if (s != SHL_OK) { free_bank(b); return s; }
+  *out = b;
+  return SHL_OK;
+}
+
+shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_levels, int full,
+                           int device, shl_bank** out) {
+  if (!out) return fail(SHL_EINVAL, "out is NULL");
+  *out = nullptr;
+  shl_status s = check_size(rows, cols);
+  if (s != SHL_OK) return s;
+  shl::HostBank hb;
+  const char* msg = shl::build_shearlet_bank(rows, cols, n_scales, shear_levels, full, &hb);
+  if (msg && *msg) return fail(SHL_EINVAL, msg);
+  shl_bank* b = new shl_bank();
+  b->device = device; b->N = rows; b->M = cols; b->Mh = cols / 2 + 1; b->K = hb.K;
+  b->spectra = std::move(hb.spectra);
+  b->idx = std::move(hb.idx);
+  s = upload_bank(b);
+  if (s != SHL_OK) { free_bank(b); return s; }
+  *out = b;
+  return SHL_OK;
+}
+
+shl_status shl_bank_destroy(shl_bank* bank) {
+  if (!bank) return SHL_OK;
+  if (bank->device < 0) { free_bank(bank); return SHL_OK; }
+  DevGuard g(bank->device);
+  free_bank(bank);
+  return SHL_OK;
+}
+
+shl_status shl_bank_query(const shl_bank* b, int* K, int* rows, int* cols) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  if (K) *K = b->K;
+  if (rows) *rows = b->N;
+  if (cols) *cols = b->M;
+  return SHL_OK;
+}
+
+shl_status shl_bank_copy_info(const shl_bank* b, int* idx, double* rms, double* spectra,
+                              double* dual_w) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  if (idx) std::memcpy(idx, b->idx.data(), b->idx.size() * sizeof(int));
+  if (rms) std::memcpy(rms, b->rms.data(), b->rms.size() * sizeof(double));
+  if (spectra) std::memcpy(spectra, b->spectra.data(), b->spectra.size() * sizeof(double));
+  if (dual_w) std::memcpy(dual_w, b->dual_w.data(), b->dual_w.size() * sizeof(double));
+  return SHL_OK;
+}
+
+shl_status shl_workspace_size(const shl_bank* b, shl_op op, int batch, size_t* bytes) {
+  if (!b || !bytes) return fail(SHL_EINVAL, "bank and bytes must be non-NULL");
+  if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
+  if (op != SHL_OP_DECOMPOSE && op != SHL_OP_RECONSTRUCT) return fail(SHL_EINVAL, "bad op");
+  *bytes = batch == 0 ? 0 : ws_need(b, batch);
+  return SHL_OK;
+}
+
+shl_status shl_decompose(const shl_bank* b, const float* x, int batch, void* coeffs,
+                         shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream) {
+  return decompose_impl(b, shl::IN_F32, x, nullptr, nullptr, batch, coeffs, dtype, flags, ws,
+                        ws_bytes, stream);
+}
+
+shl_status shl_decompose_masked(const shl_bank* b, const float* f_masked,
+                                const unsigned char* mask, const float* f_est, int batch,
+                                void* coeffs, shl_dtype dtype, void* ws, size_t ws_bytes,
+                                void* stream) {
+  return decompose_impl(b, shl::IN_MASKED, f_masked, mask, f_est, batch, coeffs, dtype, 0, ws,
+                        ws_bytes, stream);
+}
+
+shl_status shl_reconstruct(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                           const float* thresh, float* x_out, void* ws, size_t ws_bytes,
+                           void* stream) {
+  return reconstruct_impl(b, coeffs, dtype, batch, thresh, x_out, ws, ws_bytes, stream, true);
+}
+
+shl_status shl_adjoint(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                       const float* thresh, float* x_out, void* ws, size_t ws_bytes,
+                       void* stream) {
+  return reconstruct_impl(b, coeffs, dtype, batch, thresh, x_out, ws, ws_bytes, stream, false);
+}
+
+shl_status shl_subband_absmax(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                              int by_rms, float* out, void* stream) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
+  if (batch == 0) return SHL_OK;
+  if (b->device < 0) return fail(SHL_EINVAL, "bank was created host-only (device < 0)");
+  if (!coeffs || !out || !aligned16(coeffs)) return fail(SHL_EINVAL, "bad coeffs / out pointer");
+  DevGuard g(b->device);
+  cudaError_t e;
+  {
+    Launch L_("absmax", static_cast<cudaStream_t>(stream));
+    e = shl::launch_absmax(coeffs, dtype == SHL_BF16, batch * b->K, b->K, (size_t)b->N * b->M,
+                           by_rms ? b->dRms : nullptr, out, static_cast<cudaStream_t>(stream));
+  }
+  if (e) return cuda_fail(e, "absmax");
+  return SHL_OK;
+}
+
+long long shl_launch_count(void) { return g_launches.load(); }
+
+shl_status shl_profile_enable(int on) {
+  g_profile.store(on ? 1 : 0);
+  return SHL_OK;
+}
+
+shl_status shl_profile_read(char* buf, size_t len) {
+  std::vector<ProfRec> recs;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    recs.swap(g_prof);
+  }
+  std::map<std::string, std::pair<long long, double>> agg;
+  cudaError_t err = cudaSuccess;
+  for (auto& r : recs) {
+    float ms = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, r.a, r.b);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    auto& slot = agg[r.name];
+    slot.first += 1;
+    slot.second += ms;
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  std::string js = "{";
+  bool first = true;
+  for (auto& kv : agg) {
+    char tmp[160];
+    std::snprintf(tmp, sizeof tmp, "%s\"%s\": {\"launches\": %lld, \"ms\": %.6f}",
+                  first ? "" : ", ", kv.first.c_str(), kv.second.first, kv.second.second);
+    js += tmp;
+    first = false;
+  }
+  js += "}";
+  if (buf && len) {
+    std::strncpy(buf, js.c_str(), len - 1);
+    buf[len - 1] = 0;
+  }
+  if (err != cudaSuccess) return cuda_fail(err, "shl_profile_read");
+  if (js.size() + 1 > len) return fail(SHL_EINVAL, "buffer too small for the profile summary");
+  return SHL_OK;
+}
+
+shl_status shl_sync(void* stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e) return cuda_fail(e, "shl_sync");
+  return SHL_OK;
+}
+
+}  // extern "C"

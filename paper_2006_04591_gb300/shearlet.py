@@ -1,0 +1,325 @@
+"""Thin Python binding of libshearlet (include/shearlet.h).
+
+Functions carry the C names and only marshal arguments: torch tensors become
+device pointers, the current torch stream becomes the cudaStream_t.  Every
+step of the transform runs in the CUDA library; if it is missing or fails to
+load, the calls raise -- there is no CPU fallback.
+
+:class:`Bank` is a convenience owner of a bank handle that allocates output
+and workspace tensors with torch.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+import numpy as np
+
+from . import _build
+
+SHL_F32, SHL_BF16 = 0, 1
+SHL_DUAL_WEIGHTED = 1
+SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT = 0, 1
+HEADER = os.path.join(os.path.dirname(_build.PKG), "include", "shearlet.h")
+
+_lib = None
+
+
+class ShearletError(RuntimeError):
+    def __init__(self, fn, status, detail):
+        super().__init__("%s failed: status %d (%s)" % (fn, status, detail))
+        self.status = status
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load libshearlet.so (built in-tree by ``_build.build()``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError("libshearlet.so is not built: run __graft_entry__.build() "
+                           "or python -m paper_2006_04591_gb300._build")
+    L = ctypes.CDLL(_build.LIB)
+    vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+    P = ctypes.POINTER
+    sig = {
+        "shl_abi_version": (i, []),
+        "shl_status_str": (ctypes.c_char_p, [i]),
+        "shl_last_error_detail": (ctypes.c_char_p, []),
+        "shl_bank_create": (i, [i, i, i, vp, i, i, P(vp)]),
+        "shl_bank_create_from_spectra": (i, [i, i, i, vp, vp, i, P(vp)]),
+        "shl_bank_destroy": (i, [vp]),
+        "shl_bank_query": (i, [vp, P(i), P(i), P(i)]),
+        "shl_bank_copy_info": (i, [vp, vp, vp, vp, vp]),
+        "shl_workspace_size": (i, [vp, i, i, P(sz)]),
+        "shl_decompose": (i, [vp, vp, i, vp, i, i, vp, sz, vp]),
+        "shl_decompose_masked": (i, [vp, vp, vp, vp, i, vp, i, vp, sz, vp]),
+        "shl_reconstruct": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
+        "shl_adjoint": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
+        "shl_subband_absmax": (i, [vp, vp, i, i, i, vp, vp]),
+        "shl_sync": (i, [vp]),
+        "shl_launch_count": (ctypes.c_longlong, []),
+        "shl_profile_enable": (i, [i]),
+        "shl_profile_read": (i, [ctypes.c_char_p, sz]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _lib = L
+    return L
+
+
+def header_symbols() -> list[str]:
+    """Function names declared in include/shearlet.h."""
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(shl_\w+)\s*\(", txt, re.M)))
+
+
+def _check(fn, status):
+    if status != 0:
+        L = lib()
+        raise ShearletError(fn, status, "%s: %s" % (L.shl_status_str(status).decode(),
+                                                     L.shl_last_error_detail().decode()))
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream, device):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dtype_code(dt):
+    import torch
+    if dt == torch.float32:
+        return SHL_F32
+    if dt == torch.bfloat16:
+        return SHL_BF16
+    raise ValueError("coefficients must be float32 or bfloat16, got %s" % dt)
+
+
+# ------------------------------------------------------------ C-named calls
+def shl_bank_create(rows, cols, n_scales, shear_levels=None, full=0, device=0):
+    h = ctypes.c_void_p()
+    lv = None
+    if shear_levels is not None:
+        arr = (ctypes.c_int * len(shear_levels))(*shear_levels)
+        lv = ctypes.cast(arr, ctypes.c_void_p)
+    _check("shl_bank_create", lib().shl_bank_create(rows, cols, n_scales, lv, int(full), device,
+                                                    ctypes.byref(h)))
+    return h
+
+
+def shl_bank_create_from_spectra(spectra, idx=None, device=0):
+    S = np.ascontiguousarray(spectra, dtype=np.float64)
+    K, N, M = S.shape
+    ip = None
+    if idx is not None:
+        I = np.ascontiguousarray(idx, dtype=np.int32)
+        ip = I.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    _check("shl_bank_create_from_spectra",
+           lib().shl_bank_create_from_spectra(N, M, K, S.ctypes.data_as(ctypes.c_void_p), ip,
+                                              device, ctypes.byref(h)))
+    return h
+
+
+def shl_bank_destroy(h):
+    _check("shl_bank_destroy", lib().shl_bank_destroy(h))
+
+
+def shl_bank_query(h):
+    K, r, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check("shl_bank_query", lib().shl_bank_query(h, ctypes.byref(K), ctypes.byref(r),
+                                                  ctypes.byref(c)))
+    return K.value, r.value, c.value
+
+
+def shl_bank_copy_info(h, spectra=True, dual_w=True):
+    K, N, M = shl_bank_query(h)
+    idx = np.zeros((K, 3), np.int32)
+    rms = np.zeros(K, np.float64)
+    S = np.zeros((K, N, M), np.float64) if spectra else None
+    W = np.zeros((N, M), np.float64) if dual_w else None
+    cp = lambda a: None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+    _check("shl_bank_copy_info", lib().shl_bank_copy_info(h, cp(idx), cp(rms), cp(S), cp(W)))
+    return {"idx": idx, "rms": rms, "spectra": S, "dual_w": W}
+
+
+def shl_workspace_size(h, op, batch):
+    n = ctypes.c_size_t()
+    _check("shl_workspace_size", lib().shl_workspace_size(h, op, batch, ctypes.byref(n)))
+    return n.value
+
+
+def shl_decompose(h, x, batch, coeffs, dtype, flags, ws, stream=None):
+    _check("shl_decompose", lib().shl_decompose(
+        h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _ptr(ws), ws.numel() * ws.element_size(),
+        _stream(stream, x.device)))
+
+
+def shl_decompose_masked(h, f_masked, mask, f_est, batch, coeffs, dtype, ws, stream=None):
+    _check("shl_decompose_masked", lib().shl_decompose_masked(
+        h, _ptr(f_masked), _ptr(mask), _ptr(f_est), batch, _ptr(coeffs), dtype, _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream, f_masked.device)))
+
+
+def shl_reconstruct(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
+    _check("shl_reconstruct", lib().shl_reconstruct(
+        h, _ptr(coeffs), dtype, batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+
+
+def shl_adjoint(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
+    _check("shl_adjoint", lib().shl_adjoint(
+        h, _ptr(coeffs), dtype, batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+
+
+def shl_subband_absmax(h, coeffs, dtype, batch, by_rms, out, stream=None):
+    _check("shl_subband_absmax", lib().shl_subband_absmax(
+        h, _ptr(coeffs), dtype, batch, int(by_rms), _ptr(out), _stream(stream, out.device)))
+
+
+def shl_sync(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    _check("shl_sync", lib().shl_sync(ctypes.c_void_p(s.cuda_stream)))
+
+
+def shl_launch_count():
+    return int(lib().shl_launch_count())
+
+
+def shl_profile_enable(on):
+    _check("shl_profile_enable", lib().shl_profile_enable(int(on)))
+
+
+def shl_profile_read():
+    import json
+    buf = ctypes.create_string_buffer(1 << 16)
+    _check("shl_profile_read", lib().shl_profile_read(buf, len(buf)))
+    return json.loads(buf.value.decode())
+
+
+# ------------------------------------------------------------- convenience
+class Bank:
+    """Owner of a filter-bank handle on one CUDA device."""
+
+    def __init__(self, handle, device):
+        self.handle = handle
+        self.device = device
+        self.K, self.rows, self.cols = shl_bank_query(handle)
+        info = shl_bank_copy_info(handle, spectra=False, dual_w=False)
+        self.idx, self.rms = info["idx"], info["rms"]
+        self._rms_dev = None
+
+    @classmethod
+    def create(cls, rows, cols, n_scales, shear_levels=None, full=False, device=0):
+        return cls(shl_bank_create(rows, cols, n_scales, shear_levels, full, device), device)
+
+    @classmethod
+    def from_spectra(cls, spectra, idx=None, device=0):
+        return cls(shl_bank_create_from_spectra(spectra, idx, device), device)
+
+    def info(self):
+        return shl_bank_copy_info(self.handle)
+
+    def close(self):
+        if self.handle is not None:
+            shl_bank_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def rms_device(self):
+        import torch
+        if self._rms_dev is None:
+            self._rms_dev = torch.tensor(self.rms, dtype=torch.float32,
+                                         device="cuda:%d" % self.device)
+        return self._rms_dev
+
+    def workspace(self, op, batch):
+        import torch
+        n = shl_workspace_size(self.handle, op, batch)
+        return torch.empty(max(n, 16), dtype=torch.uint8, device="cuda:%d" % self.device)
+
+    def _check_images(self, x):
+        if x.dim() != 3 or x.shape[1:] != (self.rows, self.cols):
+            raise ValueError("expected [B, %d, %d] images, got %s" % (self.rows, self.cols,
+                                                                     tuple(x.shape)))
+        if not x.is_cuda or not x.is_contiguous():
+            raise ValueError("images must be contiguous CUDA tensors")
+
+    def decompose(self, x, dtype=None, dual=False, out=None, ws=None):
+        import torch
+        dtype = dtype or torch.float32
+        x = x.contiguous()
+        self._check_images(x)
+        B = x.shape[0]
+        c = out if out is not None else torch.empty((B, self.K, self.rows, self.cols),
+                                                    dtype=dtype, device=x.device)
+        ws = ws if ws is not None else self.workspace(SHL_OP_DECOMPOSE, B)
+        shl_decompose(self.handle, x, B, c, _dtype_code(c.dtype),
+                      SHL_DUAL_WEIGHTED if dual else 0, ws)
+        return c
+
+    def decompose_masked(self, f_masked, mask_u8, f_est, dtype=None, out=None, ws=None):
+        import torch
+        dtype = dtype or torch.float32
+        self._check_images(f_masked)
+        B = f_masked.shape[0]
+        c = out if out is not None else torch.empty((B, self.K, self.rows, self.cols),
+                                                    dtype=dtype, device=f_masked.device)
+        ws = ws if ws is not None else self.workspace(SHL_OP_DECOMPOSE, B)
+        shl_decompose_masked(self.handle, f_masked, mask_u8, f_est, B, c,
+                             _dtype_code(c.dtype), ws)
+        return c
+
+    def _rec(self, fn, c, thresh, out, ws):
+        import torch
+        c = c.contiguous()
+        if c.dim() != 4 or c.shape[1:] != (self.K, self.rows, self.cols):
+            raise ValueError("expected [B, K, N, M] coefficients, got %s" % (tuple(c.shape),))
+        B = c.shape[0]
+        x = out if out is not None else torch.empty((B, self.rows, self.cols),
+                                                    dtype=torch.float32, device=c.device)
+        if thresh is not None:
+            thresh = thresh.to(device=c.device, dtype=torch.float32).contiguous()
+            if thresh.shape != (B, self.K):
+                raise ValueError("thresholds must be [B, K]")
+        ws = ws if ws is not None else self.workspace(SHL_OP_RECONSTRUCT, B)
+        fn(self.handle, c, _dtype_code(c.dtype), B, thresh, x, ws)
+        return x
+
+    def reconstruct(self, c, thresh=None, out=None, ws=None):
+        return self._rec(shl_reconstruct, c, thresh, out, ws)
+
+    def adjoint(self, c, thresh=None, out=None, ws=None):
+        return self._rec(shl_adjoint, c, thresh, out, ws)
+
+    def subband_absmax(self, c, by_rms=False, out=None):
+        import torch
+        B = c.shape[0]
+        out = out if out is not None else torch.empty((B, self.K), dtype=torch.float32,
+                                                      device=c.device)
+        shl_subband_absmax(self.handle, c.contiguous(), _dtype_code(c.dtype), B, by_rms, out)
+        return out

@@ -1,0 +1,88 @@
+"""C-ABI checks that need no GPU: the library builds, loads, exports every
+symbol the header declares, validates arguments before touching CUDA, and
+its float64 host filter-bank builder matches the oracle's construction."""
+
+import ctypes
+
+import numpy as np
+import pytest
+
+from oracle import bank as Bk
+from paper_2006_04591_gb300 import _build, shearlet as S
+
+
+@pytest.fixture(scope="module")
+def L():
+    _build.build()
+    return S.lib()
+
+
+def test_exports_every_header_symbol(L):
+    names = S.header_symbols()
+    assert len(names) >= 14
+    raw = ctypes.CDLL(S.library_path())
+    missing = [n for n in names if not hasattr(raw, n)]
+    assert missing == []
+
+
+def test_version_and_status_strings(L):
+    assert L.shl_abi_version() == 1
+    assert L.shl_status_str(0) == b"ok"
+    assert L.shl_status_str(4) == b"unsupported"
+
+
+def test_unsupported_sizes_rejected(L):
+    h = ctypes.c_void_p()
+    for r, c in [(15, 16), (16, 24), (8, 16), (4096, 16), (16, 0)]:
+        st = L.shl_bank_create(r, c, 2, None, 0, -1, ctypes.byref(h))
+        assert st == 4 and not h.value
+    st = L.shl_bank_create(16, 16, 2, None, 0, -1, None)
+    assert st == 1
+
+
+def test_non_even_spectrum_rejected():
+    rng = np.random.default_rng(0)
+    G = rng.standard_normal((2, 16, 16))
+    with pytest.raises(S.ShearletError) as e:
+        S.shl_bank_create_from_spectra(G, device=-1)
+    assert e.value.status == 1
+
+
+def test_zero_dual_weight_rejected():
+    G = np.zeros((1, 16, 16))
+    G[0, 0, 0] = 1.0
+    with pytest.raises(S.ShearletError) as e:
+        S.shl_bank_create_from_spectra(G, device=-1)
+    assert e.value.status == 1
+
+
+def test_host_only_bank_rejects_transform_calls(L):
+    h = S.shl_bank_create(16, 16, 1, device=-1)
+    n = ctypes.c_size_t()
+    assert L.shl_workspace_size(h, 0, 2, ctypes.byref(n)) == 0 and n.value > 0
+    fake = ctypes.c_void_p(1 << 20)
+    st = L.shl_decompose(h, fake, 1, fake, 0, 0, fake, n.value, None)
+    assert st == 1 and b"host-only" in L.shl_last_error_detail()
+    assert L.shl_workspace_size(None, 0, 1, ctypes.byref(n)) == 1
+    S.shl_bank_destroy(h)
+
+
+@pytest.mark.parametrize("rows,cols,J,levels,full", [
+    (32, 32, 2, None, False), (64, 64, 3, None, False), (32, 64, 2, None, False),
+    (64, 32, 2, [1, 2], True), (32, 32, 1, [0], False),
+])
+def test_host_bank_builder_matches_oracle(rows, cols, J, levels, full):
+    h = S.shl_bank_create(rows, cols, J, levels, full, device=-1)
+    info = S.shl_bank_copy_info(h)
+    S.shl_bank_destroy(h)
+    ref = Bk.shearlet_bank(rows, cols, J, levels, full)
+    assert info["spectra"].shape == ref["spectra"].shape
+    np.testing.assert_array_equal(info["idx"], ref["idx"])
+    np.testing.assert_allclose(info["spectra"], ref["spectra"], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(info["rms"], ref["rms"], rtol=1e-12)
+    np.testing.assert_allclose(info["dual_w"], ref["dual_w"], rtol=1e-12)
+
+
+def test_bad_levels_rejected():
+    with pytest.raises(S.ShearletError):
+        S.shl_bank_create(32, 32, 2, [1, 7], device=-1)
