@@ -26,8 +26,8 @@ struct shl_bank {
   std::vector<int> idx;          // [K][3]
   std::vector<double> rms;       // [K]
   std::vector<double> dual_w;    // [N][M]
-  float* dG = nullptr;           // [K][N][Mh] half spectra
-  float* dInvW = nullptr;        // [N][Mh]
+  float* dG = nullptr;           // [K][Mh][N] half spectra, transposed
+  float* dInvW = nullptr;        // [Mh][N]
   float2* dTw = nullptr;         // [TW_P]
   float* dRms = nullptr;         // [K]
 };
@@ -94,8 +94,8 @@ struct Launch {
 int stage_subbands(const shl_bank* b) {
   static const double mb = [] {
     const char* e = std::getenv("SHL_STAGE_MB");
-    double v = e ? std::atof(e) : 32.0;
-    return v > 0 ? v : 32.0;
+    double v = e ? std::atof(e) : 56.0;
+    return v > 0 ? v : 56.0;
   }();
   const double per = double(b->N) * b->Mh * sizeof(float2);
   int s = (int)(mb * 1024.0 * 1024.0 / per);
@@ -140,9 +140,9 @@ shl_status upload_bank(shl_bank* b) {
   for (int i = 0; i < K; ++i)
     for (int y = 0; y < N; ++y)
       for (int x = 0; x < Mh; ++x)
-        hG[((size_t)i * N + y) * Mh + x] = (float)b->spectra[((size_t)i * N + y) * M + x];
+        hG[((size_t)i * Mh + x) * N + y] = (float)b->spectra[((size_t)i * N + y) * M + x];
   for (int y = 0; y < N; ++y)
-    for (int x = 0; x < Mh; ++x) hW[(size_t)y * Mh + x] = (float)(1.0 / b->dual_w[(size_t)y * M + x]);
+    for (int x = 0; x < Mh; ++x) hW[(size_t)x * N + y] = (float)(1.0 / b->dual_w[(size_t)y * M + x]);
   for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
   std::vector<float2> hT(shl::TW_P);
   const double PI = 3.14159265358979323846264338327950288;
@@ -199,39 +199,46 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   if (flags & ~SHL_DUAL_WEIGHTED) return fail(SHL_EINVAL, "unknown flags");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int N = b->N, M = b->M, K = b->K;
+  const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
   float2* X = static_cast<float2*>(ws);
   float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
                                         align256((size_t)batch * plane_bytes(b)));
   cudaError_t e;
-  shl::RowR2CArgs ra{};
-  ra.in = x; ra.mask = mask; ra.fest = fest; ra.out = X; ra.thresh = nullptr;
-  ra.tw = b->dTw; ra.nlines = batch * N; ra.N = N;
-  { Launch L_("rows_r2c_image", st); e = shl::launch_rows_r2c(M, mode, false, ra, st); }
-  if (e) return cuda_fail(e, "rows_r2c");
-  shl::ColArgs ca{};
-  ca.data = X; ca.Mh = b->Mh; ca.tw = b->dTw; ca.K = K;
-  { Launch L_("cols_fwd", st); e = shl::launch_cols(N, shl::COL_FWD, ca, batch, st); }
-  if (e) return cuda_fail(e, "cols_fwd");
+  {
+    Launch L_("rows_r2c_image", st);
+    e = shl::launch_rows_r2c_t(M, mode, false, x, mask, fest, nullptr, X, N, batch, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "rows_r2c_image");
+  {
+    Launch L_("lines_fwd_image", st);
+    e = shl::launch_lines_fwd(N, X, batch * Mh, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "lines_fwd_image");
   const int total = batch * K, S = stage_subbands(b);
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  const float scale = (float)(1.0 / (double(N) * M));
   for (int s0 = 0; s0 < total; s0 += S) {
     const int Sc = std::min(S, total - s0);
-    shl::ColArgs d{};
-    d.data = X; d.out = Z; d.G = b->dG; d.invW = (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr;
-    d.tw = b->dTw; d.scale = (float)(1.0 / (double(N) * M)); d.Mh = b->Mh; d.K = K;
-    d.s0 = s0; d.S = Sc;
-    { Launch L_("cols_dec_inv", st); e = shl::launch_cols(N, shl::COL_DEC_INV, d, Sc, st); }
-    if (e) return cuda_fail(e, "cols_dec_inv");
-    shl::RowC2RArgs c{};
-    c.in = Z; c.out = static_cast<char*>(coeffs) + (size_t)s0 * N * M * esz;
-    c.tw = b->dTw; c.nlines = Sc * N;
-    { Launch L_("rows_c2r_coeffs", st); e = shl::launch_rows_c2r(M, dtype == SHL_BF16, c, st); }
-    if (e) return cuda_fail(e, "rows_c2r");
+    {
+      Launch L_("dec_lines", st);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr,
+                                scale, Mh, K, s0, Sc, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "dec_lines");
+    {
+      Launch L_("rows_c2r_coeffs", st);
+      e = shl::launch_rows_c2r_t(M, dtype == SHL_BF16, Z,
+                                 static_cast<char*>(coeffs) + (size_t)s0 * N * M * esz, N, Sc,
+                                 b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "rows_c2r_coeffs");
   }
   return SHL_OK;
 }
 
+// Reconstruction chunks: whole images when the staging area holds K
+// subbands, otherwise filter ranges inside one image (partial sums are
+// carried in the accumulator plane of that image).
 shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
                             const float* thresh, float* x_out, void* ws, size_t ws_bytes,
                             void* stream, bool weights) {
@@ -244,41 +251,44 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
   if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int N = b->N, M = b->M, K = b->K;
+  const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
   float2* A = static_cast<float2*>(ws);
   float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
                                         align256((size_t)batch * plane_bytes(b)));
   const int total = batch * K, S = stage_subbands(b);
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  const float scale = (float)(1.0 / (double(N) * M));
   cudaError_t e;
-  for (int s0 = 0; s0 < total; s0 += S) {
-    const int Sc = std::min(S, total - s0);
-    shl::RowR2CArgs ra{};
-    ra.in = static_cast<const char*>(coeffs) + (size_t)s0 * N * M * esz;
-    ra.out = Z; ra.thresh = thresh ? thresh + s0 : nullptr; ra.tw = b->dTw;
-    ra.nlines = Sc * N; ra.N = N;
+  for (int s0 = 0; s0 < total;) {
+    int Sc;
+    if (S >= K) {
+      Sc = std::min((S / K) * K, total - s0);
+    } else {
+      const int img_end = (s0 / K + 1) * K;
+      Sc = std::min(S, img_end - s0);
+    }
     {
       Launch L_("rows_r2c_coeffs", st);
-      e = shl::launch_rows_r2c(M, dtype == SHL_BF16 ? shl::IN_BF16 : shl::IN_F32,
-                               thresh != nullptr, ra, st);
+      e = shl::launch_rows_r2c_t(M, dtype == SHL_BF16 ? shl::IN_BF16 : shl::IN_F32,
+                                 thresh != nullptr,
+                                 static_cast<const char*>(coeffs) + (size_t)s0 * N * M * esz,
+                                 nullptr, nullptr, thresh ? thresh + s0 : nullptr, Z, N, Sc,
+                                 b->dTw, st);
     }
-    if (e) return cuda_fail(e, "rows_r2c");
-    shl::ColArgs ca{};
-    ca.in = Z; ca.acc = A; ca.G = b->dG; ca.tw = b->dTw; ca.Mh = b->Mh; ca.K = K;
-    ca.s0 = s0; ca.S = Sc; ca.b_lo = s0 / K;
-    const int b_hi = (s0 + Sc - 1) / K;
-    { Launch L_("cols_rec_acc", st); e = shl::launch_cols(N, shl::COL_REC_ACC, ca, b_hi - ca.b_lo + 1, st); }
-    if (e) return cuda_fail(e, "cols_rec_acc");
+    if (e) return cuda_fail(e, "rows_r2c_coeffs");
+    {
+      Launch L_("rec_lines", st);
+      e = shl::launch_rec_lines(N, Z, A, b->dG, weights ? b->dInvW : nullptr, scale, Mh, K, s0,
+                                Sc, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "rec_lines");
+    s0 += Sc;
   }
-  shl::ColArgs f{};
-  f.data = A; f.invW = weights ? b->dInvW : nullptr; f.tw = b->dTw;
-  f.scale = (float)(1.0 / (double(N) * M)); f.Mh = b->Mh; f.K = K;
-  { Launch L_("cols_final_inv", st); e = shl::launch_cols(N, shl::COL_FINAL_INV, f, batch, st); }
-  if (e) return cuda_fail(e, "cols_final");
-  shl::RowC2RArgs c{};
-  c.in = A; c.out = x_out; c.tw = b->dTw; c.nlines = batch * N;
-  { Launch L_("rows_c2r_image", st); e = shl::launch_rows_c2r(M, false, c, st); }
-  if (e) return cuda_fail(e, "rows_c2r");
+  {
+    Launch L_("rows_c2r_image", st);
+    e = shl::launch_rows_c2r_t(M, false, A, x_out, N, batch, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "rows_c2r_image");
   return SHL_OK;
 }
 

@@ -1,0 +1,508 @@
+// fast.cu - the transform kernels (warp-line design).
+//
+// Half spectra live "transposed": H[kx][ky], kx = 0..M/2 (Mh lines), ky =
+// 0..N-1 contiguous, so that every column transform runs along one
+// contiguous line owned by a lane group (line_fft).  Row transforms run on
+// the image rows and move to / from the transposed layout through a
+// 16-row shared-memory tile, whose global side is written or read as 128-byte
+// runs.
+//
+//   k_rows_r2c_t  real rows (image, masked image or coefficients with
+//                 threshold-on-read) -> R2C -> H planes.
+//   k_rows_c2r_t  H planes -> C2R -> real rows (float32 or bfloat16).
+//   k_lines_fwd   in-place forward column FFT of H lines (image spectra).
+//   k_dec_lines   Z = IFFT_y(G_i * scale [* 1/W] * X_b) per subband line
+//                 (the filter multiply of Sec. 3.4 fused into the load).
+//   k_rec_lines   one CTA per (image, kx): lane groups split the chunk's
+//                 filters, FFT_y each staged line, multiply by G_i, sum in
+//                 registers; the CTA adds the partial sums in fixed order,
+//                 and on the image's last chunk applies scale [* 1/W] and the
+//                 inverse column FFT (Sec. 3.4 reconstruction).
+//
+// Real-row packing: z[n] = x[2n] + i x[2n+1] with a length-M/2 complex FFT
+// and the conjugate-pair split (see rows.cu of the reference derivation):
+//   R2C: X[k] = E[k] + exp(-2 pi i k/M) O[k], E = (Z[k] + conj Z[L-k]) / 2,
+//        O = -i (Z[k] - conj Z[L-k]) / 2, X[L] = Re Z[0] - Im Z[0];
+//   C2R: Z[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k/M) (X[k] - conj X[L-k]),
+//        x[2n] + i x[2n+1] = unnormalised IFFT_L(Z)[n] (= M times the
+//        normalised inverse; 1/(N M) is folded into filter or weight factors).
+#include "warp_fft.cuh"
+
+namespace shl {
+
+constexpr int TILE_R = 16;          // rows per transpose tile
+constexpr int TILE_P = TILE_R + 1;  // padded tile pitch (float2)
+
+// ------------------------------------------------------------------ rows
+template <int LOG_M>
+struct RowsT {
+  static constexpr int M = 1 << LOG_M;
+  static constexpr int L = M / 2;
+  static constexpr int R = LineRadix<L>::R;
+  using C = LineCfg<L, R>;
+  static constexpr int T = C::T;
+  static constexpr int LPC = (TILE_R * T) >= 32 ? TILE_R : 32 / T;  // lines incl. idle ones
+  static constexpr int THREADS = LPC * T;
+  static constexpr int Mh = L + 1;
+  // the transpose tile reuses the line buffers (separated by __syncthreads)
+  static constexpr size_t LINES = (size_t)LPC * C::WORDS, TILE = (size_t)Mh * TILE_P;
+  static constexpr size_t SMEM = sizeof(float2) * (LINES > TILE ? LINES : TILE);
+};
+
+struct RowsTArgs {
+  const void* in;            // [nsub][N][M] reals, or f_masked
+  const uint8_t* mask;       // masked mode
+  const float* fest;         // masked mode
+  const float* thresh;       // [nsub] or null
+  float2* out;               // [nsub][Mh][N]
+  const float2* tw;
+  int N, nsub;
+};
+
+template <int LOG_M, int INM, bool THRESH>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS) k_rows_r2c_t(RowsTArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh;
+  extern __shared__ float2 smem[];
+  float2* tile = smem;
+  const int tid = threadIdx.x;
+  const int r = tid / T, j = tid % T;
+  const int tiles_per_sub = a.N / TILE_R;
+  const int s = blockIdx.x / tiles_per_sub;
+  const int y0 = (blockIdx.x % tiles_per_sub) * TILE_R;
+  const bool valid = r < TILE_R;
+  float2* line = smem + (size_t)r * P::C::WORDS;
+
+  float tau = 0.f;
+  if (THRESH) tau = __ldg(a.thresh + s);
+  const size_t row_off = ((size_t)s * a.N + y0 + (valid ? r : 0)) * P::M;
+
+  float2 v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const size_t off = row_off + 2 * (size_t)(j + u * T);
+    float2 z = make_float2(0.f, 0.f);
+    if (valid) {
+      if constexpr (INM == IN_F32) {
+        z = __ldcs(reinterpret_cast<const float2*>(static_cast<const float*>(a.in) + off));
+      } else if constexpr (INM == IN_BF16) {
+        unsigned int w = __ldcs(reinterpret_cast<const unsigned int*>(
+            static_cast<const __nv_bfloat16*>(a.in) + off));
+        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
+        z = __bfloat1622float2(h);
+      } else {
+        const float2 fm = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(a.in) + off));
+        const float2 fe = __ldg(reinterpret_cast<const float2*>(a.fest + off));
+        const uchar2 mk = *reinterpret_cast<const uchar2*>(a.mask + off);
+        z.x = mk.x ? fm.x : fe.x;   // mask (f_masked - f_est) + f_est, mask in {0, 1}
+        z.y = mk.y ? fm.y : fe.y;
+      }
+      if (THRESH) {
+        if (fabsf(z.x) < tau) z.x = 0.f;
+        if (fabsf(z.y) < tau) z.y = 0.f;
+      }
+    }
+    v[u] = z;
+  }
+
+  line_fft<L, R, -1>(v, line, j, 1 + r, a.tw);
+
+  // conjugate-pair split needs Z[L - k]: publish the natural-order line
+  group_sync<T>(1 + r);
+#pragma unroll
+  for (int u = 0; u < R; ++u) line[pad_index(j + u * T, P::C::LOG_R)] = v[u];
+  group_sync<T>(1 + r);
+  const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], used by lane j == 0
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int k = j + u * T;
+    const float2 A = v[u];
+    const float2 B = line[pad_index((L - k) & (L - 1), P::C::LOG_R)];
+    const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+    const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+    v[u] = cadd(E, cmul(O, twiddle<-1>(a.tw, k, LOG_M)));
+  }
+  __syncthreads();                       // line buffers become the tile
+  if (valid) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) tile[(j + u * T) * TILE_P + r] = v[u];
+    if (j == 0) tile[L * TILE_P + r] = nyq;
+  }
+  __syncthreads();
+  float2* out = a.out + (size_t)s * Mh * a.N + y0;
+  for (int idx = tid; idx < Mh * TILE_R; idx += P::THREADS) {
+    const int kx = idx / TILE_R, rr = idx % TILE_R;
+    out[(size_t)kx * a.N + rr] = tile[kx * TILE_P + rr];
+  }
+}
+
+struct RowsTC2RArgs {
+  const float2* in;          // [nsub][Mh][N]
+  void* out;                 // [nsub][N][M]
+  const float2* tw;
+  int N, nsub;
+};
+
+template <int LOG_M, bool BF16OUT>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS) k_rows_c2r_t(RowsTC2RArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh;
+  extern __shared__ float2 smem[];
+  float2* tile = smem;
+  const int tid = threadIdx.x;
+  const int r = tid / T, j = tid % T;
+  const int tiles_per_sub = a.N / TILE_R;
+  const int s = blockIdx.x / tiles_per_sub;
+  const int y0 = (blockIdx.x % tiles_per_sub) * TILE_R;
+  const bool valid = r < TILE_R;
+  float2* line = smem + (size_t)r * P::C::WORDS;
+
+  const float2* in = a.in + (size_t)s * Mh * a.N + y0;
+  for (int idx = tid; idx < Mh * TILE_R; idx += P::THREADS) {
+    const int kx = idx / TILE_R, rr = idx % TILE_R;
+    tile[kx * TILE_P + rr] = in[(size_t)kx * a.N + rr];
+  }
+  __syncthreads();
+
+  float2 v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int k = j + u * T;
+    float2 z = make_float2(0.f, 0.f);
+    if (valid) {
+      const float2 A = tile[k * TILE_P + r];
+      const float2 B = tile[(L - k) * TILE_P + r];
+      const float2 S = make_float2(A.x + B.x, A.y - B.y);
+      const float2 D = make_float2(A.x - B.x, A.y + B.y);
+      const float2 wd = cmul(D, twiddle<+1>(a.tw, k, LOG_M));
+      z = make_float2(S.x - wd.y, S.y + wd.x);
+    }
+    v[u] = z;
+  }
+  __syncthreads();                       // the tile becomes the line buffers
+
+  line_fft<L, R, +1>(v, line, j, 1 + r, a.tw);
+
+  if (!valid) return;
+  const size_t base = ((size_t)s * a.N + y0 + r) * P::M;
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int p = j + u * T;
+    if constexpr (BF16OUT) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
+      __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(a.out) + base + 2 * p),
+             *reinterpret_cast<unsigned int*>(&h));
+    } else {
+      __stcs(reinterpret_cast<float2*>(static_cast<float*>(a.out) + base + 2 * p), v[u]);
+    }
+  }
+}
+
+// ----------------------------------------------------------------- lines
+template <int LOG_N>
+struct LinesT {
+  static constexpr int N = 1 << LOG_N;
+  static constexpr int R = LineRadix<N>::R;
+  using C = LineCfg<N, R>;
+  static constexpr int T = C::T;
+  static constexpr int THREADS = 256;
+  static constexpr int NG = THREADS / T;              // lane groups per CTA
+  static constexpr size_t SMEM_LINES = sizeof(float2) * (size_t)NG * C::WORDS;
+};
+
+struct LinesArgs {
+  float2* data;              // FWD: [nlines][N] in place; DEC: image spectra [B][Mh][N]
+  float2* out;               // DEC: staging [S][Mh][N]
+  const float* G;            // [K][Mh][N]
+  const float* invW;         // [Mh][N] or null
+  const float2* tw;
+  float scale;
+  int Mh, K, s0, nlines;
+};
+
+template <int LOG_N>
+__global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
+  using P = LinesT<LOG_N>;
+  constexpr int T = P::T, R = P::R, N = P::N;
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / T, j = threadIdx.x % T;
+  float2* line = smem + (size_t)g * P::C::WORDS;
+  for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
+    float2* d = a.data + (size_t)q * N;
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = d[j + u * T];
+    line_fft<N, R, -1>(v, line, j, 1 + g, a.tw);
+#pragma unroll
+    for (int u = 0; u < R; ++u) d[j + u * T] = v[u];
+  }
+}
+
+template <int LOG_N>
+__global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
+  using P = LinesT<LOG_N>;
+  constexpr int T = P::T, R = P::R, N = P::N;
+  extern __shared__ float2 smem[];
+  const int g = threadIdx.x / T, j = threadIdx.x % T;
+  float2* line = smem + (size_t)g * P::C::WORDS;
+  for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
+    const int sl = q / a.Mh, kx = q - sl * a.Mh;
+    const int s = a.s0 + sl;
+    const int b = s / a.K, i = s - b * a.K;
+    const float2* X = a.data + ((size_t)b * a.Mh + kx) * N;
+    const float* G = a.G + ((size_t)i * a.Mh + kx) * N;
+    const float* W = a.invW ? a.invW + (size_t)kx * N : nullptr;
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      float gv = __ldg(G + j + u * T) * a.scale;
+      if (W) gv *= __ldg(W + j + u * T);
+      v[u] = cscale(X[j + u * T], gv);
+    }
+    line_fft<N, R, +1>(v, line, j, 1 + g, a.tw);
+    float2* out = a.out + (size_t)q * N;
+#pragma unroll
+    for (int u = 0; u < R; ++u) out[j + u * T] = v[u];
+  }
+}
+
+struct RecLinesArgs {
+  const float2* stage;       // [Sc][Mh][N] row spectra of the chunk's subbands
+  float2* acc;               // [B][Mh][N] partial sums, then the image lines
+  const float* G;            // [K][Mh][N]
+  const float* invW;         // [Mh][N] or null (adjoint)
+  const float2* tw;
+  float scale;
+  int Mh, K, s0, Sc, b_lo;
+};
+
+template <int LOG_N>
+__global__ void __launch_bounds__(256) k_rec_lines(RecLinesArgs a) {
+  using P = LinesT<LOG_N>;
+  constexpr int T = P::T, R = P::R, N = P::N, NG = P::NG;
+  extern __shared__ float2 smem[];
+  float2* red = smem + (size_t)NG * P::C::WORDS;     // [NG][N] partial sums
+  const int g = threadIdx.x / T, j = threadIdx.x % T;
+  float2* line = smem + (size_t)g * P::C::WORDS;
+  const int kx = blockIdx.x;
+  const int b = a.b_lo + blockIdx.y;
+  const int s_begin = max(a.s0, b * a.K), s_end = min(a.s0 + a.Sc, (b + 1) * a.K);
+  const bool first = s_begin == b * a.K, last = s_end == (b + 1) * a.K;
+
+  float2 acc[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) acc[u] = make_float2(0.f, 0.f);
+  for (int s = s_begin + g; s < s_end; s += NG) {
+    const float2* U = a.stage + ((size_t)(s - a.s0) * a.Mh + kx) * N;
+    const float* G = a.G + ((size_t)(s - b * a.K) * a.Mh + kx) * N;
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = U[j + u * T];
+    line_fft<N, R, -1>(v, line, j, 1 + g, a.tw);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const float gv = __ldg(G + j + u * T);
+      acc[u].x = fmaf(gv, v[u].x, acc[u].x);
+      acc[u].y = fmaf(gv, v[u].y, acc[u].y);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < R; ++u) red[(size_t)g * N + j + u * T] = acc[u];
+  __syncthreads();
+  float2* A = a.acc + ((size_t)b * a.Mh + kx) * N;
+  for (int p = threadIdx.x; p < N; p += P::THREADS) {
+    float2 sum = red[p];
+    for (int q = 1; q < NG; ++q) sum = cadd(sum, red[(size_t)q * N + p]);
+    if (!first) sum = cadd(A[p], sum);
+    if (!last) {
+      A[p] = sum;
+    } else {
+      float sc = a.scale;
+      if (a.invW) sc *= __ldg(a.invW + (size_t)kx * N + p);
+      red[p] = cscale(sum, sc);
+    }
+  }
+  if (!last) return;
+  __syncthreads();
+  if (g == 0) {
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = red[j + u * T];
+    line_fft<N, R, +1>(v, line, j, 1, a.tw);
+#pragma unroll
+    for (int u = 0; u < R; ++u) A[j + u * T] = v[u];
+  }
+}
+
+// --------------------------------------------------------------- launch
+template <typename K>
+static cudaError_t prep(K kernel, size_t smem) {
+  if (smem > 48 * 1024)
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  return cudaSuccess;
+}
+
+static int sm_count() {
+  static int n = [] {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+  }();
+  return n;
+}
+
+template <int LOG_M>
+static cudaError_t r2c_t(InMode mode, bool th, const RowsTArgs& a, cudaStream_t st) {
+  using P = RowsT<LOG_M>;
+  const int grid = a.nsub * (a.N / TILE_R);
+  if (grid == 0) return cudaSuccess;
+  cudaError_t e;
+#define SHL_LAUNCH(INM, TH)                                                         \
+  do {                                                                              \
+    if ((e = prep(k_rows_r2c_t<LOG_M, INM, TH>, P::SMEM))) return e;                \
+    k_rows_r2c_t<LOG_M, INM, TH><<<grid, P::THREADS, P::SMEM, st>>>(a);              \
+  } while (0)
+  if (mode == IN_MASKED) SHL_LAUNCH(IN_MASKED, false);
+  else if (mode == IN_BF16) { if (th) SHL_LAUNCH(IN_BF16, true); else SHL_LAUNCH(IN_BF16, false); }
+  else { if (th) SHL_LAUNCH(IN_F32, true); else SHL_LAUNCH(IN_F32, false); }
+#undef SHL_LAUNCH
+  return cudaGetLastError();
+}
+
+template <int LOG_M>
+static cudaError_t c2r_t(bool bf16, const RowsTC2RArgs& a, cudaStream_t st) {
+  using P = RowsT<LOG_M>;
+  const int grid = a.nsub * (a.N / TILE_R);
+  if (grid == 0) return cudaSuccess;
+  cudaError_t e;
+  if (bf16) {
+    if ((e = prep(k_rows_c2r_t<LOG_M, true>, P::SMEM))) return e;
+    k_rows_c2r_t<LOG_M, true><<<grid, P::THREADS, P::SMEM, st>>>(a);
+  } else {
+    if ((e = prep(k_rows_c2r_t<LOG_M, false>, P::SMEM))) return e;
+    k_rows_c2r_t<LOG_M, false><<<grid, P::THREADS, P::SMEM, st>>>(a);
+  }
+  return cudaGetLastError();
+}
+
+template <int LOG_N>
+static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra, int grid_y,
+                           cudaStream_t st) {
+  using P = LinesT<LOG_N>;
+  cudaError_t e;
+  if (mode == 0 || mode == 1) {
+    if (a.nlines == 0) return cudaSuccess;
+    const int grid = std::min((a.nlines + P::NG - 1) / P::NG, sm_count() * 8);
+    if (mode == 0) {
+      if ((e = prep(k_lines_fwd<LOG_N>, P::SMEM_LINES))) return e;
+      k_lines_fwd<LOG_N><<<grid, P::THREADS, P::SMEM_LINES, st>>>(a);
+    } else {
+      if ((e = prep(k_dec_lines<LOG_N>, P::SMEM_LINES))) return e;
+      k_dec_lines<LOG_N><<<grid, P::THREADS, P::SMEM_LINES, st>>>(a);
+    }
+  } else {
+    const size_t sm = P::SMEM_LINES + sizeof(float2) * (size_t)P::NG * P::N;
+    if ((e = prep(k_rec_lines<LOG_N>, sm))) return e;
+    k_rec_lines<LOG_N><<<dim3(ra.Mh, grid_y), P::THREADS, sm, st>>>(ra);
+  }
+  return cudaGetLastError();
+}
+
+#define SHL_SWITCH_LOG(LOGV, CALL)                 \
+  switch (LOGV) {                                  \
+    case 4: return CALL(4);                        \
+    case 5: return CALL(5);                        \
+    case 6: return CALL(6);                        \
+    case 7: return CALL(7);                        \
+    case 8: return CALL(8);                        \
+    case 9: return CALL(9);                        \
+    case 10: return CALL(10);                      \
+    case 11: return CALL(11);                      \
+    default: return cudaErrorInvalidValue;         \
+  }
+
+cudaError_t launch_rows_r2c_t(int M, InMode mode, bool thresh, const void* in, const uint8_t* mask,
+                              const float* fest, const float* th, float2* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st) {
+  RowsTArgs a{in, mask, fest, th, out, tw, N, nsub};
+#define CALL(X) r2c_t<X>(mode, thresh, a, st)
+  SHL_SWITCH_LOG(ilog2(M), CALL)
+#undef CALL
+}
+
+cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st) {
+  RowsTC2RArgs a{in, out, tw, N, nsub};
+#define CALL(X) c2r_t<X>(bf16, a, st)
+  SHL_SWITCH_LOG(ilog2(M), CALL)
+#undef CALL
+}
+
+cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, cudaStream_t st) {
+  LinesArgs a{};
+  a.data = data; a.nlines = nlines; a.tw = tw;
+  RecLinesArgs ra{};
+#define CALL(X) lines_t<X>(0, a, ra, 0, st)
+  SHL_SWITCH_LOG(ilog2(N), CALL)
+#undef CALL
+}
+
+cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
+                             float scale, int Mh, int K, int s0, int S, const float2* tw,
+                             cudaStream_t st) {
+  LinesArgs a{};
+  a.data = const_cast<float2*>(X); a.out = out; a.G = G; a.invW = invW; a.tw = tw;
+  a.scale = scale; a.Mh = Mh; a.K = K; a.s0 = s0; a.nlines = S * Mh;
+  RecLinesArgs ra{};
+#define CALL(X) lines_t<X>(1, a, ra, 0, st)
+  SHL_SWITCH_LOG(ilog2(N), CALL)
+#undef CALL
+}
+
+cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
+                             const float* invW, float scale, int Mh, int K, int s0, int Sc,
+                             const float2* tw, cudaStream_t st) {
+  LinesArgs a{};
+  RecLinesArgs ra{stage, acc, G, invW, tw, scale, Mh, K, s0, Sc, s0 / K};
+  const int b_hi = (s0 + Sc - 1) / K;
+  const int gy = Sc > 0 ? b_hi - ra.b_lo + 1 : 0;
+  if (gy == 0) return cudaSuccess;
+#define CALL(X) lines_t<X>(2, a, ra, gy, st)
+  SHL_SWITCH_LOG(ilog2(N), CALL)
+#undef CALL
+}
+
+// Per-subband max |c| (optionally divided by RMS_i): one CTA per subband.
+template <bool BF16>
+__global__ void __launch_bounds__(256) k_absmax(const void* coeffs, int K, size_t elems,
+                                                const float* rms, float* out) {
+  const int s = blockIdx.x;
+  float m = 0.f;
+  if constexpr (BF16) {
+    const __nv_bfloat16* p = static_cast<const __nv_bfloat16*>(coeffs) + (size_t)s * elems;
+    for (size_t e = threadIdx.x; e < elems; e += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(p[e])));
+  } else {
+    const float* p = static_cast<const float*>(coeffs) + (size_t)s * elems;
+    for (size_t e = threadIdx.x; e < elems; e += blockDim.x) m = fmaxf(m, fabsf(__ldg(p + e)));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+    out[s] = rms ? r / rms[s % K] : r;
+  }
+}
+
+cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
+                          const float* rms, float* out, cudaStream_t st) {
+  if (nsub == 0) return cudaSuccess;
+  if (bf16) k_absmax<true><<<nsub, 256, 0, st>>>(coeffs, K, elems, rms, out);
+  else k_absmax<false><<<nsub, 256, 0, st>>>(coeffs, K, elems, rms, out);
+  return cudaGetLastError();
+}
+
+}  // namespace shl

@@ -19,50 +19,20 @@ enum InMode : int {
   IN_MASKED = 2,   // u = mask * (f_masked - f_est) + f_est, float32
 };
 
-// Column pass modes (see cols kernels).
-enum ColMode : int {
-  COL_FWD = 0,        // in-place forward FFT of image spectra
-  COL_DEC_INV = 1,    // (X_b * G_i * scale [* invW]) -> inverse FFT -> staging
-  COL_REC_ACC = 2,    // forward FFT of staged rows, * G_i, sum over i -> acc
-  COL_FINAL_INV = 3,  // acc * scale [* invW] -> inverse FFT, in place
-};
-
-struct RowR2CArgs {
-  const void* in;          // [nlines][M] reals (float or bf16), or f_masked
-  const uint8_t* mask;     // IN_MASKED only
-  const float* fest;       // IN_MASKED only
-  float2* out;             // [nlines][Mh]
-  const float* thresh;     // per subband (line / N), may be null
-  const float2* tw;
-  int nlines;
-  int N;                   // lines per subband (image rows)
-};
-
-struct RowC2RArgs {
-  const float2* in;        // [nlines][Mh]
-  void* out;               // [nlines][M] float or bf16
-  const float2* tw;
-  int nlines;
-};
-
-struct ColArgs {
-  float2* data;            // FWD / FINAL_INV: [B][N][Mh] in place; DEC_INV: image spectra
-  float2* out;             // DEC_INV: staging [S][N][Mh]
-  const float2* in;        // REC_ACC: staging rows [S][N][Mh]
-  float2* acc;             // REC_ACC: accumulators [B][N][Mh]
-  const float* G;          // [K][N][Mh]
-  const float* invW;       // [N][Mh] or null
-  const float2* tw;
-  float scale;
-  int Mh, K;
-  int s0, S;               // subband range of the chunk (DEC_INV / REC_ACC)
-  int b_lo;                // REC_ACC: first image of the chunk
-};
-
-cudaError_t launch_rows_r2c(int M, InMode mode, bool thresh, const RowR2CArgs& a,
-                            cudaStream_t st);
-cudaError_t launch_rows_c2r(int M, bool bf16_out, const RowC2RArgs& a, cudaStream_t st);
-cudaError_t launch_cols(int N, ColMode mode, const ColArgs& a, int grid_y, cudaStream_t st);
+// Launchers of fast.cu.  Half-spectrum planes are stored transposed,
+// [Mh][N] with Mh = M/2 + 1 and the N column-frequency values contiguous.
+cudaError_t launch_rows_r2c_t(int M, InMode mode, bool thresh, const void* in, const uint8_t* mask,
+                              const float* fest, const float* th, float2* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st);
+cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st);
+cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, cudaStream_t st);
+cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
+                             float scale, int Mh, int K, int s0, int S, const float2* tw,
+                             cudaStream_t st);
+cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
+                             const float* invW, float scale, int Mh, int K, int s0, int Sc,
+                             const float2* tw, cudaStream_t st);
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st);
 

@@ -1,0 +1,105 @@
+// warp_fft.cuh - FFT of one contiguous line by a group of lanes.
+//
+// A line of L complex values is held by T = L/R lanes (R <= 32), lane j
+// owning positions j + u*T.  Groups of T <= 32 lanes sit inside one warp and
+// synchronise with __syncwarp; a group of 64 lanes (two warps) uses a named
+// barrier.  The Stockham exchanges go through a group-private shared-memory
+// line padded by one slot every R elements, which keeps every exchange free
+// of bank conflicts.  No CTA-wide barrier is involved, so warps of a CTA
+// progress independently.
+#pragma once
+
+#include "fft_core.cuh"
+
+namespace shl {
+
+template <int L, int R>
+struct LineCfg {
+  static constexpr int T = L / R;                   // lanes per line
+  static constexpr int LOG_L = ilog2(L), LOG_R = ilog2(R);
+  static constexpr int NFULL = LOG_L / LOG_R;
+  static constexpr int LAST = 1 << (LOG_L - NFULL * LOG_R);
+  static constexpr int WORDS = L + L / R;           // padded line in shared memory
+  static_assert(T >= 1 && T <= 64, "line group must fit two warps");
+};
+
+// Radix for a line of length L: 32 for the longest lines, else 16.
+template <int L> struct LineRadix {
+  static constexpr int R = L >= 1024 ? 32 : (L < 16 ? L : 16);
+};
+
+__device__ __forceinline__ int pad_index(int p, int logR) { return p + (p >> logR); }
+
+// Synchronise the lanes of one line group, and only those: groups that share
+// a warp may run different numbers of loop iterations, so a group narrower
+// than a warp synchronises with the mask of its own T aligned lanes.  A group
+// spanning two warps uses named barrier bar_id (1..15) over its 64 threads.
+template <int T>
+__device__ __forceinline__ void group_sync(int bar_id) {
+  if constexpr (T < 32) {
+    const unsigned lane = threadIdx.x & 31u;
+    __syncwarp(((1u << T) - 1u) << (lane & ~(unsigned)(T - 1)));
+  } else if constexpr (T == 32) {
+    __syncwarp();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(T) : "memory");
+  }
+}
+
+// In-place FFT of the line held as v[u] = x[j + u*T]; on return v[u] =
+// X[j + u*T].  SIGN = -1 forward, +1 inverse (unnormalised).  sm is the
+// group's padded line buffer (LineCfg::WORDS float2).
+template <int L, int R, int SIGN>
+__device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int bar_id,
+                                         const float2* __restrict__ tw) {
+  using C = LineCfg<L, R>;
+  constexpr int T = C::T;
+#pragma unroll
+  for (int st = 0; st < C::NFULL; ++st) {
+    const int logNs = st * C::LOG_R;
+    const int Ns = 1 << logNs;
+    if (st > 0) {
+      const int k = j & (Ns - 1);
+      if constexpr (R <= 16) {           // issue all table loads before the products
+        float2 w[R];
+#pragma unroll
+        for (int u = 1; u < R; ++u) w[u] = twiddle<SIGN>(tw, u * k, logNs + C::LOG_R);
+#pragma unroll
+        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], w[u]);
+      } else {
+#pragma unroll
+        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], twiddle<SIGN>(tw, u * k, logNs + C::LOG_R));
+      }
+    }
+    dft_reg<R, SIGN>(v);
+    if (st < C::NFULL - 1 || C::LAST > 1) {
+      const int idxD = ((j >> logNs) << (logNs + C::LOG_R)) + (j & (Ns - 1));
+      group_sync<T>(bar_id);
+#pragma unroll
+      for (int u = 0; u < R; ++u) sm[pad_index(idxD + u * Ns, C::LOG_R)] = v[u];
+      group_sync<T>(bar_id);
+#pragma unroll
+      for (int u = 0; u < R; ++u) v[u] = sm[pad_index(j + u * T, C::LOG_R)];
+    }
+  }
+  if constexpr (C::LAST > 1) {
+    constexpr int LAST = C::LAST;
+    constexpr int Q = R / LAST;
+    constexpr int logNs = C::LOG_L - ilog2(LAST);
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const int k = (j + q * T) & ((1 << logNs) - 1);
+      float2 w[LAST];
+#pragma unroll
+      for (int m = 0; m < LAST; ++m) {
+        w[m] = v[q + m * Q];
+        if (m > 0) w[m] = cmul(w[m], twiddle<SIGN>(tw, m * k, C::LOG_L));
+      }
+      dft_reg<LAST, SIGN>(w);
+#pragma unroll
+      for (int m = 0; m < LAST; ++m) v[q + m * Q] = w[m];
+    }
+  }
+}
+
+}  // namespace shl
