@@ -30,10 +30,27 @@
 
 namespace shl {
 
-constexpr int TILE_R = 16;          // rows per transpose tile
-constexpr int TILE_P = TILE_R + 1;  // padded tile pitch (float2)
 
 // ------------------------------------------------------------------ rows
+// The row kernels are persistent: each CTA walks tiles of 16 rows and keeps
+// the next tile's input landing in shared memory (cp.async, two stages)
+// while it transforms the current one.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// Copy `bytes` (multiple of 16) from gmem to smem with all threads of the CTA.
+__device__ __forceinline__ void cta_copy_async(void* dst, const void* src, int bytes, int tid,
+                                               int nthreads) {
+  char* d = static_cast<char*>(dst);
+  const char* s = static_cast<const char*>(src);
+  for (int c = tid * 16; c < bytes; c += nthreads * 16) cp_async16(d + c, s + c);
+}
+
 template <int LOG_M>
 struct RowsT {
   static constexpr int M = 1 << LOG_M;
@@ -41,12 +58,26 @@ struct RowsT {
   static constexpr int R = LineRadix<L>::R;
   using C = LineCfg<L, R>;
   static constexpr int T = C::T;
-  static constexpr int LPC = (TILE_R * T) >= 32 ? TILE_R : 32 / T;  // lines incl. idle ones
+  static constexpr int TR = M >= 2048 ? 8 : 16;   // rows per tile
+  static constexpr int TP = TR + 1;               // padded transpose-tile pitch
+  static constexpr int LPC = (TR * T) >= 32 ? TR : 32 / T;  // lines incl. idle ones
   static constexpr int THREADS = LPC * T;
   static constexpr int Mh = L + 1;
+  static constexpr int CPITCH = TR + 2;           // c2r input tile pitch (16-byte rows)
   // the transpose tile reuses the line buffers (separated by __syncthreads)
-  static constexpr size_t LINES = (size_t)LPC * C::WORDS, TILE = (size_t)Mh * TILE_P;
-  static constexpr size_t SMEM = sizeof(float2) * (LINES > TILE ? LINES : TILE);
+  static constexpr size_t LINES = (size_t)LPC * C::WORDS, TILE = (size_t)Mh * TP;
+  static constexpr size_t WORK = sizeof(float2) * (LINES > TILE ? LINES : TILE);
+  static constexpr size_t CSTAGE = sizeof(float2) * (size_t)Mh * CPITCH;
+  static constexpr size_t SMEM_CAP = 224 * 1024;
+  static constexpr int MINB = M <= 512 ? 2 : 1;    // CTAs per SM the sizes allow
+  static constexpr size_t TWB = sizeof(float2) * ((size_t)LineTw<L, R>::WORDS + L);  // twiddles
+  static constexpr int CNST = 2 * CSTAGE + WORK + TWB <= SMEM_CAP ? 2 : 1;   // c2r pipeline depth
+  static_assert(CSTAGE + WORK + TWB <= SMEM_CAP, "c2r tile does not fit shared memory");
+};
+
+template <int INM>
+struct RowInput {  // bytes of one 16-row input tile per stream
+  static constexpr int ESZ = INM == IN_BF16 ? 2 : 4;
 };
 
 struct RowsTArgs {
@@ -59,41 +90,102 @@ struct RowsTArgs {
   int N, nsub;
 };
 
-template <int LOG_M, int INM, bool THRESH>
-__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS) k_rows_r2c_t(RowsTArgs a) {
+template <int LOG_M, int INM>
+__host__ __device__ constexpr size_t r2c_stage_bytes() {
+  return INM == IN_MASKED ? (size_t)RowsT<LOG_M>::TR * (1 << LOG_M) * (4 + 4 + 1)
+                          : (size_t)RowsT<LOG_M>::TR * (1 << LOG_M) * RowInput<INM>::ESZ;
+}
+// r2c pipeline depth: 2 (double-buffered), 1, or 0 (inputs read straight
+// from global memory when even one staged tile does not fit).
+template <int LOG_M, int INM>
+__host__ __device__ constexpr int r2c_nst() {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh;
-  extern __shared__ float2 smem[];
-  float2* tile = smem;
+  constexpr size_t SB = r2c_stage_bytes<LOG_M, INM>(), REST = P::WORK + P::TWB;
+  return 2 * SB + REST <= P::SMEM_CAP ? 2 : (SB + REST <= P::SMEM_CAP ? 1 : 0);
+}
+
+template <int LOG_M, int INM>
+__device__ __forceinline__ void r2c_issue(const RowsTArgs& a, char* stage, int t, int tid) {
+  using P = RowsT<LOG_M>;
+  const int tiles_per_sub = a.N / P::TR;
+  const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
+  const size_t row0 = (size_t)s * a.N + y0;
+  constexpr int n = P::TR * P::M;
+  if constexpr (INM == IN_MASKED) {
+    cta_copy_async(stage, static_cast<const float*>(a.in) + row0 * P::M, n * 4, tid, P::THREADS);
+    cta_copy_async(stage + n * 4, a.fest + row0 * P::M, n * 4, tid, P::THREADS);
+    cta_copy_async(stage + n * 8, a.mask + row0 * P::M, n, tid, P::THREADS);
+  } else {
+    constexpr int esz = RowInput<INM>::ESZ;
+    cta_copy_async(stage, static_cast<const char*>(a.in) + row0 * P::M * esz, n * esz, tid,
+                   P::THREADS);
+  }
+}
+
+template <int LOG_M, int INM, bool THRESH>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_r2c_t(RowsTArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, M = P::M;
+  constexpr int TR = P::TR, TP = P::TP;
+  constexpr size_t SB = r2c_stage_bytes<LOG_M, INM>();
+  constexpr int NST = r2c_nst<LOG_M, INM>();
+  extern __shared__ __align__(16) float2 smem[];
+  char* stages = reinterpret_cast<char*>(smem);
+  float2* work = reinterpret_cast<float2*>(stages + (size_t)NST * SB);
+  float2* tile = work;
+  float2* twl = work + P::WORK / sizeof(float2);          // line-FFT twiddles
+  float2* ptw = twl + LineTw<L, R>::WORDS;                 // exp(-2 pi i p / M), p < L
   const int tid = threadIdx.x;
   const int r = tid / T, j = tid % T;
-  const int tiles_per_sub = a.N / TILE_R;
-  const int s = blockIdx.x / tiles_per_sub;
-  const int y0 = (blockIdx.x % tiles_per_sub) * TILE_R;
-  const bool valid = r < TILE_R;
-  float2* line = smem + (size_t)r * P::C::WORDS;
+  const bool valid = r < TR;
+  float2* line = work + (size_t)r * P::C::WORDS;
+  const int tiles_per_sub = a.N / TR;
+  const int ntiles = a.nsub * tiles_per_sub;
 
-  float tau = 0.f;
-  if (THRESH) tau = __ldg(a.thresh + s);
-  const size_t row_off = ((size_t)s * a.N + y0 + (valid ? r : 0)) * P::M;
+  LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
+  for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  if (NST == 2 && blockIdx.x < ntiles) r2c_issue<LOG_M, INM>(a, stages, blockIdx.x, tid);
+  cp_async_commit();
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    if constexpr (NST > 0) {
+      const int tn = NST == 2 ? t + gridDim.x : t;
+      if (tn < ntiles) r2c_issue<LOG_M, INM>(a, stages + ((k + 1) % NST) * SB, tn, tid);
+      cp_async_commit();
+      if (NST == 2) cp_async_wait1(); else cp_async_wait0();
+    }
+    __syncthreads();
+    const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
+    // tile input: staged in shared memory, or the global rows themselves
+    const char* cur = NST > 0 ? stages + (k % (NST > 0 ? NST : 1)) * SB : nullptr;
+    const size_t grow0 = ((size_t)s * a.N + y0) * M;
+    constexpr int n = TR * M;
+    const float2* src_f = NST > 0 ? reinterpret_cast<const float2*>(cur)
+                                  : reinterpret_cast<const float2*>(static_cast<const float*>(a.in) + grow0);
+    const __nv_bfloat162* src_h = NST > 0 ? reinterpret_cast<const __nv_bfloat162*>(cur)
+                                          : reinterpret_cast<const __nv_bfloat162*>(
+                                                static_cast<const __nv_bfloat16*>(a.in) + grow0);
+    const float2* src_e = NST > 0 ? reinterpret_cast<const float2*>(cur + n * 4)
+                                  : reinterpret_cast<const float2*>(a.fest ? a.fest + grow0 : nullptr);
+    const uchar2* src_m = NST > 0 ? reinterpret_cast<const uchar2*>(cur + n * 8)
+                                  : reinterpret_cast<const uchar2*>(a.mask ? a.mask + grow0 : nullptr);
+    float tau = 0.f;
+    if (THRESH) tau = __ldg(a.thresh + s);
+    const int rr = valid ? r : 0;
 
-  float2 v[R];
+    float2 v[R];
 #pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const size_t off = row_off + 2 * (size_t)(j + u * T);
-    float2 z = make_float2(0.f, 0.f);
-    if (valid) {
+    for (int u = 0; u < R; ++u) {
+      const int p = j + u * T;
+      float2 z;
       if constexpr (INM == IN_F32) {
-        z = __ldcs(reinterpret_cast<const float2*>(static_cast<const float*>(a.in) + off));
+        z = src_f[rr * (M / 2) + p];
       } else if constexpr (INM == IN_BF16) {
-        unsigned int w = __ldcs(reinterpret_cast<const unsigned int*>(
-            static_cast<const __nv_bfloat16*>(a.in) + off));
-        __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&w);
-        z = __bfloat1622float2(h);
+        z = __bfloat1622float2(src_h[rr * (M / 2) + p]);
       } else {
-        const float2 fm = __ldg(reinterpret_cast<const float2*>(static_cast<const float*>(a.in) + off));
-        const float2 fe = __ldg(reinterpret_cast<const float2*>(a.fest + off));
-        const uchar2 mk = *reinterpret_cast<const uchar2*>(a.mask + off);
+        const float2 fm = src_f[rr * (M / 2) + p];
+        const float2 fe = src_e[rr * (M / 2) + p];
+        const uchar2 mk = src_m[rr * (M / 2) + p];
         z.x = mk.x ? fm.x : fe.x;   // mask (f_masked - f_est) + f_est, mask in {0, 1}
         z.y = mk.y ? fm.y : fe.y;
       }
@@ -101,39 +193,41 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS) k_rows_r2c_t(RowsTArgs 
         if (fabsf(z.x) < tau) z.x = 0.f;
         if (fabsf(z.y) < tau) z.y = 0.f;
       }
+      v[u] = valid ? z : make_float2(0.f, 0.f);
     }
-    v[u] = z;
-  }
 
-  line_fft<L, R, -1>(v, line, j, 1 + r, a.tw);
+    line_fft<L, R, -1>(v, line, j, 1 + r, twl);
 
-  // conjugate-pair split needs Z[L - k]: publish the natural-order line
-  group_sync<T>(1 + r);
+    // conjugate-pair split needs Z[L - k]: publish the natural-order line
+    group_sync<T>(1 + r);
 #pragma unroll
-  for (int u = 0; u < R; ++u) line[pad_index(j + u * T, P::C::LOG_R)] = v[u];
-  group_sync<T>(1 + r);
-  const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], used by lane j == 0
+    for (int u = 0; u < R; ++u) line[pad_index(j + u * T, P::C::LOG_R)] = v[u];
+    group_sync<T>(1 + r);
+    const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], kept by lane j == 0
 #pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int k = j + u * T;
-    const float2 A = v[u];
-    const float2 B = line[pad_index((L - k) & (L - 1), P::C::LOG_R)];
-    const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-    const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-    v[u] = cadd(E, cmul(O, twiddle<-1>(a.tw, k, LOG_M)));
-  }
-  __syncthreads();                       // line buffers become the tile
-  if (valid) {
+    for (int u = 0; u < R; ++u) {
+      const int kk = j + u * T;
+      const float2 A = v[u];
+      const float2 B = line[pad_index((L - kk) & (L - 1), P::C::LOG_R)];
+      const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+      const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+      v[u] = cadd(E, cmul(O, ptw[kk]));
+    }
+    __syncthreads();                       // line buffers become the tile
+    if (valid) {
 #pragma unroll
-    for (int u = 0; u < R; ++u) tile[(j + u * T) * TILE_P + r] = v[u];
-    if (j == 0) tile[L * TILE_P + r] = nyq;
+      for (int u = 0; u < R; ++u) tile[(j + u * T) * TP + r] = v[u];
+      if (j == 0) tile[L * TP + r] = nyq;
+    }
+    __syncthreads();
+    float2* out = a.out + (size_t)s * Mh * a.N + y0;
+    for (int idx = tid; idx < Mh * TR; idx += P::THREADS) {
+      const int kx = idx / TR, q = idx % TR;
+      out[(size_t)kx * a.N + q] = tile[kx * TP + q];
+    }
+    __syncthreads();                       // tile / stage reuse
   }
-  __syncthreads();
-  float2* out = a.out + (size_t)s * Mh * a.N + y0;
-  for (int idx = tid; idx < Mh * TILE_R; idx += P::THREADS) {
-    const int kx = idx / TILE_R, rr = idx % TILE_R;
-    out[(size_t)kx * a.N + rr] = tile[kx * TILE_P + rr];
-  }
+  cp_async_wait0();
 }
 
 struct RowsTC2RArgs {
@@ -143,59 +237,82 @@ struct RowsTC2RArgs {
   int N, nsub;
 };
 
-template <int LOG_M, bool BF16OUT>
-__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS) k_rows_c2r_t(RowsTC2RArgs a) {
+template <int LOG_M>
+__device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, int t, int tid) {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh;
-  extern __shared__ float2 smem[];
-  float2* tile = smem;
+  const int tiles_per_sub = a.N / P::TR;
+  const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
+  const float2* in = a.in + (size_t)s * P::Mh * a.N + y0;
+  constexpr int CH = P::TR / 2;                       // 16-byte chunks per kx row
+  for (int c = tid; c < P::Mh * CH; c += P::THREADS) {
+    const int kx = c / CH, q = c % CH;
+    cp_async16(stage + kx * P::CPITCH + 2 * q, in + (size_t)kx * a.N + 2 * q);
+  }
+}
+
+template <int LOG_M, bool BF16OUT>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_c2r_t(RowsTC2RArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, CP = P::CPITCH, TR = P::TR, NST = P::CNST;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stages = smem;
+  float2* work = smem + NST * (P::CSTAGE / sizeof(float2));
+  float2* twl = work + P::WORK / sizeof(float2);
+  float2* ptw = twl + LineTw<L, R>::WORDS;
   const int tid = threadIdx.x;
   const int r = tid / T, j = tid % T;
-  const int tiles_per_sub = a.N / TILE_R;
-  const int s = blockIdx.x / tiles_per_sub;
-  const int y0 = (blockIdx.x % tiles_per_sub) * TILE_R;
-  const bool valid = r < TILE_R;
-  float2* line = smem + (size_t)r * P::C::WORDS;
+  const bool valid = r < TR;
+  const int rr = valid ? r : 0;
+  float2* line = work + (size_t)r * P::C::WORDS;
+  const int tiles_per_sub = a.N / TR;
+  const int ntiles = a.nsub * tiles_per_sub;
+  constexpr size_t SW = P::CSTAGE / sizeof(float2);
 
-  const float2* in = a.in + (size_t)s * Mh * a.N + y0;
-  for (int idx = tid; idx < Mh * TILE_R; idx += P::THREADS) {
-    const int kx = idx / TILE_R, rr = idx % TILE_R;
-    tile[kx * TILE_P + rr] = in[(size_t)kx * a.N + rr];
-  }
-  __syncthreads();
+  LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
+  for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M>(a, stages, blockIdx.x, tid);
+  cp_async_commit();
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int tn = NST == 2 ? t + gridDim.x : t;
+    if (tn < ntiles) c2r_issue<LOG_M>(a, stages + ((k + 1) % NST) * SW, tn, tid);
+    cp_async_commit();
+    if (NST == 2) cp_async_wait1(); else cp_async_wait0();
+    __syncthreads();
+    const float2* tile = stages + (k % NST) * SW;
+    const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
 
-  float2 v[R];
+    float2 v[R];
 #pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int k = j + u * T;
-    float2 z = make_float2(0.f, 0.f);
-    if (valid) {
-      const float2 A = tile[k * TILE_P + r];
-      const float2 B = tile[(L - k) * TILE_P + r];
+    for (int u = 0; u < R; ++u) {
+      const int kk = j + u * T;
+      const float2 A = tile[kk * CP + rr];
+      const float2 B = tile[(L - kk) * CP + rr];
       const float2 S = make_float2(A.x + B.x, A.y - B.y);
       const float2 D = make_float2(A.x - B.x, A.y + B.y);
-      const float2 wd = cmul(D, twiddle<+1>(a.tw, k, LOG_M));
-      z = make_float2(S.x - wd.y, S.y + wd.x);
+      const float2 wd = cmulc(D, ptw[kk]);        // D * exp(+2 pi i k / M)
+      v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
     }
-    v[u] = z;
-  }
-  __syncthreads();                       // the tile becomes the line buffers
 
-  line_fft<L, R, +1>(v, line, j, 1 + r, a.tw);
+    line_fft<L, R, +1>(v, line, j, 1 + r, twl);
 
-  if (!valid) return;
-  const size_t base = ((size_t)s * a.N + y0 + r) * P::M;
+    if (valid) {
+      const size_t base = ((size_t)s * a.N + y0 + r) * P::M;
 #pragma unroll
-  for (int u = 0; u < R; ++u) {
-    const int p = j + u * T;
-    if constexpr (BF16OUT) {
-      __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
-      __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(a.out) + base + 2 * p),
-             *reinterpret_cast<unsigned int*>(&h));
-    } else {
-      __stcs(reinterpret_cast<float2*>(static_cast<float*>(a.out) + base + 2 * p), v[u]);
+      for (int u = 0; u < R; ++u) {
+        const int p = j + u * T;
+        if constexpr (BF16OUT) {
+          __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
+          __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(a.out) + base + 2 * p),
+                 *reinterpret_cast<unsigned int*>(&h));
+        } else {
+          __stcs(reinterpret_cast<float2*>(static_cast<float*>(a.out) + base + 2 * p), v[u]);
+        }
+      }
     }
+    __syncthreads();                       // stage reuse
   }
+  cp_async_wait0();
 }
 
 // ----------------------------------------------------------------- lines
@@ -208,6 +325,7 @@ struct LinesT {
   static constexpr int THREADS = 256;
   static constexpr int NG = THREADS / T;              // lane groups per CTA
   static constexpr size_t SMEM_LINES = sizeof(float2) * (size_t)NG * C::WORDS;
+  static constexpr size_t TWB = sizeof(float2) * (size_t)LineTw<N, R>::WORDS;
 };
 
 struct LinesArgs {
@@ -227,12 +345,15 @@ __global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
   extern __shared__ float2 smem[];
   const int g = threadIdx.x / T, j = threadIdx.x % T;
   float2* line = smem + (size_t)g * P::C::WORDS;
+  float2* twl = smem + (size_t)P::NG * P::C::WORDS;
+  LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  __syncthreads();
   for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
     float2* d = a.data + (size_t)q * N;
     float2 v[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) v[u] = d[j + u * T];
-    line_fft<N, R, -1>(v, line, j, 1 + g, a.tw);
+    line_fft<N, R, -1>(v, line, j, 1 + g, twl);
 #pragma unroll
     for (int u = 0; u < R; ++u) d[j + u * T] = v[u];
   }
@@ -245,6 +366,9 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   extern __shared__ float2 smem[];
   const int g = threadIdx.x / T, j = threadIdx.x % T;
   float2* line = smem + (size_t)g * P::C::WORDS;
+  float2* twl = smem + (size_t)P::NG * P::C::WORDS;
+  LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  __syncthreads();
   for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
     const int sl = q / a.Mh, kx = q - sl * a.Mh;
     const int s = a.s0 + sl;
@@ -259,7 +383,7 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
       if (W) gv *= __ldg(W + j + u * T);
       v[u] = cscale(X[j + u * T], gv);
     }
-    line_fft<N, R, +1>(v, line, j, 1 + g, a.tw);
+    line_fft<N, R, +1>(v, line, j, 1 + g, twl);
     float2* out = a.out + (size_t)q * N;
 #pragma unroll
     for (int u = 0; u < R; ++u) out[j + u * T] = v[u];
@@ -277,13 +401,16 @@ struct RecLinesArgs {
 };
 
 template <int LOG_N>
-__global__ void __launch_bounds__(256) k_rec_lines(RecLinesArgs a) {
+__global__ void __launch_bounds__(256, 2) k_rec_lines(RecLinesArgs a) {
   using P = LinesT<LOG_N>;
   constexpr int T = P::T, R = P::R, N = P::N, NG = P::NG;
   extern __shared__ float2 smem[];
   float2* red = smem + (size_t)NG * P::C::WORDS;     // [NG][N] partial sums
+  float2* twl = red + (size_t)NG * N;
   const int g = threadIdx.x / T, j = threadIdx.x % T;
   float2* line = smem + (size_t)g * P::C::WORDS;
+  LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  __syncthreads();
   const int kx = blockIdx.x;
   const int b = a.b_lo + blockIdx.y;
   const int s_begin = max(a.s0, b * a.K), s_end = min(a.s0 + a.Sc, (b + 1) * a.K);
@@ -298,7 +425,7 @@ __global__ void __launch_bounds__(256) k_rec_lines(RecLinesArgs a) {
     float2 v[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) v[u] = U[j + u * T];
-    line_fft<N, R, -1>(v, line, j, 1 + g, a.tw);
+    line_fft<N, R, -1>(v, line, j, 1 + g, twl);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       const float gv = __ldg(G + j + u * T);
@@ -328,7 +455,7 @@ __global__ void __launch_bounds__(256) k_rec_lines(RecLinesArgs a) {
     float2 v[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) v[u] = red[j + u * T];
-    line_fft<N, R, +1>(v, line, j, 1, a.tw);
+    line_fft<N, R, +1>(v, line, j, 1, twl);
 #pragma unroll
     for (int u = 0; u < R; ++u) A[j + u * T] = v[u];
   }
@@ -355,13 +482,15 @@ static int sm_count() {
 template <int LOG_M>
 static cudaError_t r2c_t(InMode mode, bool th, const RowsTArgs& a, cudaStream_t st) {
   using P = RowsT<LOG_M>;
-  const int grid = a.nsub * (a.N / TILE_R);
-  if (grid == 0) return cudaSuccess;
+  const int ntiles = a.nsub * (a.N / P::TR);
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = std::min(ntiles, sm_count() * P::MINB);
   cudaError_t e;
 #define SHL_LAUNCH(INM, TH)                                                         \
   do {                                                                              \
-    if ((e = prep(k_rows_r2c_t<LOG_M, INM, TH>, P::SMEM))) return e;                \
-    k_rows_r2c_t<LOG_M, INM, TH><<<grid, P::THREADS, P::SMEM, st>>>(a);              \
+    const size_t sm = r2c_nst<LOG_M, INM>() * r2c_stage_bytes<LOG_M, INM>() + P::WORK + P::TWB; \
+    if ((e = prep(k_rows_r2c_t<LOG_M, INM, TH>, sm))) return e;                     \
+    k_rows_r2c_t<LOG_M, INM, TH><<<grid, P::THREADS, sm, st>>>(a);                   \
   } while (0)
   if (mode == IN_MASKED) SHL_LAUNCH(IN_MASKED, false);
   else if (mode == IN_BF16) { if (th) SHL_LAUNCH(IN_BF16, true); else SHL_LAUNCH(IN_BF16, false); }
@@ -373,15 +502,17 @@ static cudaError_t r2c_t(InMode mode, bool th, const RowsTArgs& a, cudaStream_t 
 template <int LOG_M>
 static cudaError_t c2r_t(bool bf16, const RowsTC2RArgs& a, cudaStream_t st) {
   using P = RowsT<LOG_M>;
-  const int grid = a.nsub * (a.N / TILE_R);
-  if (grid == 0) return cudaSuccess;
+  const int ntiles = a.nsub * (a.N / P::TR);
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = std::min(ntiles, sm_count() * P::MINB);
+  const size_t sm = P::CNST * P::CSTAGE + P::WORK + P::TWB;
   cudaError_t e;
   if (bf16) {
-    if ((e = prep(k_rows_c2r_t<LOG_M, true>, P::SMEM))) return e;
-    k_rows_c2r_t<LOG_M, true><<<grid, P::THREADS, P::SMEM, st>>>(a);
+    if ((e = prep(k_rows_c2r_t<LOG_M, true>, sm))) return e;
+    k_rows_c2r_t<LOG_M, true><<<grid, P::THREADS, sm, st>>>(a);
   } else {
-    if ((e = prep(k_rows_c2r_t<LOG_M, false>, P::SMEM))) return e;
-    k_rows_c2r_t<LOG_M, false><<<grid, P::THREADS, P::SMEM, st>>>(a);
+    if ((e = prep(k_rows_c2r_t<LOG_M, false>, sm))) return e;
+    k_rows_c2r_t<LOG_M, false><<<grid, P::THREADS, sm, st>>>(a);
   }
   return cudaGetLastError();
 }
@@ -394,15 +525,16 @@ static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra,
   if (mode == 0 || mode == 1) {
     if (a.nlines == 0) return cudaSuccess;
     const int grid = std::min((a.nlines + P::NG - 1) / P::NG, sm_count() * 8);
+    const size_t sm = P::SMEM_LINES + P::TWB;
     if (mode == 0) {
-      if ((e = prep(k_lines_fwd<LOG_N>, P::SMEM_LINES))) return e;
-      k_lines_fwd<LOG_N><<<grid, P::THREADS, P::SMEM_LINES, st>>>(a);
+      if ((e = prep(k_lines_fwd<LOG_N>, sm))) return e;
+      k_lines_fwd<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
     } else {
-      if ((e = prep(k_dec_lines<LOG_N>, P::SMEM_LINES))) return e;
-      k_dec_lines<LOG_N><<<grid, P::THREADS, P::SMEM_LINES, st>>>(a);
+      if ((e = prep(k_dec_lines<LOG_N>, sm))) return e;
+      k_dec_lines<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
     }
   } else {
-    const size_t sm = P::SMEM_LINES + sizeof(float2) * (size_t)P::NG * P::N;
+    const size_t sm = P::SMEM_LINES + sizeof(float2) * (size_t)P::NG * P::N + P::TWB;
     if ((e = prep(k_rec_lines<LOG_N>, sm))) return e;
     k_rec_lines<LOG_N><<<dim3(ra.Mh, grid_y), P::THREADS, sm, st>>>(ra);
   }

@@ -46,30 +46,73 @@ __device__ __forceinline__ void group_sync(int bar_id) {
   }
 }
 
+// Per-lane twiddles of one line FFT, staged in shared memory as [..][lane]
+// so that a lane group reads them as consecutive words (one conflict-free
+// access per stage and element) instead of scattered table loads.
+//   stages st = 1..NFULL-1: w(st, u, j) = exp(-2 pi i u (j mod Ns) / (Ns R)),
+//   last stage (radix LAST): w(q, m, j) = exp(-2 pi i m ((j + qT) mod Ns) / L).
+// Inverse transforms use the conjugates.
+template <int L, int R>
+struct LineTw {
+  using C = LineCfg<L, R>;
+  static constexpr int T = C::T;
+  static constexpr int Q = C::LAST > 1 ? R / C::LAST : 0;
+  static constexpr int STAGE_WORDS = (C::NFULL - 1) * (R - 1) * T;
+  static constexpr int LAST_WORDS = C::LAST > 1 ? Q * (C::LAST - 1) * T : 0;
+  static constexpr int WORDS = STAGE_WORDS + LAST_WORDS;
+
+  static __device__ void fill(float2* sm, const float2* __restrict__ tw, int tid, int nthreads) {
+    for (int idx = tid; idx < WORDS; idx += nthreads) {
+      int e, logD;
+      if (idx < STAGE_WORDS) {
+        const int st = 1 + idx / ((R - 1) * T);
+        const int rem = idx % ((R - 1) * T);
+        const int u = 1 + rem / T, j = rem % T;
+        const int logNs = st * C::LOG_R;
+        e = u * (j & ((1 << logNs) - 1));
+        logD = logNs + C::LOG_R;
+      } else {
+        if constexpr (C::LAST > 1) {
+          const int rem = idx - STAGE_WORDS;
+          const int qm = rem / T, j = rem % T;
+          const int q = qm / (C::LAST - 1), m = 1 + qm % (C::LAST - 1);
+          const int logNs = C::LOG_L - ilog2(C::LAST);
+          e = m * ((j + q * T) & ((1 << logNs) - 1));
+          logD = C::LOG_L;
+        } else {
+          e = 0;
+          logD = 1;
+        }
+      }
+      sm[idx] = twiddle<-1>(tw, e, logD);
+    }
+  }
+};
+
+template <int SIGN>
+__device__ __forceinline__ float2 stw(const float2* p) {
+  const float2 w = *p;
+  return SIGN < 0 ? w : make_float2(w.x, -w.y);
+}
+
 // In-place FFT of the line held as v[u] = x[j + u*T]; on return v[u] =
 // X[j + u*T].  SIGN = -1 forward, +1 inverse (unnormalised).  sm is the
-// group's padded line buffer (LineCfg::WORDS float2).
+// group's padded line buffer (LineCfg::WORDS float2); stw_sm holds the
+// staged twiddles of LineTw<L, R>.
 template <int L, int R, int SIGN>
 __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int bar_id,
-                                         const float2* __restrict__ tw) {
+                                         const float2* __restrict__ stw_sm) {
   using C = LineCfg<L, R>;
+  using W = LineTw<L, R>;
   constexpr int T = C::T;
 #pragma unroll
   for (int st = 0; st < C::NFULL; ++st) {
     const int logNs = st * C::LOG_R;
     const int Ns = 1 << logNs;
     if (st > 0) {
-      const int k = j & (Ns - 1);
-      if constexpr (R <= 16) {           // issue all table loads before the products
-        float2 w[R];
+      const float2* w = stw_sm + (st - 1) * (R - 1) * T + j;
 #pragma unroll
-        for (int u = 1; u < R; ++u) w[u] = twiddle<SIGN>(tw, u * k, logNs + C::LOG_R);
-#pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], w[u]);
-      } else {
-#pragma unroll
-        for (int u = 1; u < R; ++u) v[u] = cmul(v[u], twiddle<SIGN>(tw, u * k, logNs + C::LOG_R));
-      }
+      for (int u = 1; u < R; ++u) v[u] = cmul(v[u], stw<SIGN>(w + (u - 1) * T));
     }
     dft_reg<R, SIGN>(v);
     if (st < C::NFULL - 1 || C::LAST > 1) {
@@ -85,15 +128,14 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int 
   if constexpr (C::LAST > 1) {
     constexpr int LAST = C::LAST;
     constexpr int Q = R / LAST;
-    constexpr int logNs = C::LOG_L - ilog2(LAST);
+    const float2* wl = stw_sm + W::STAGE_WORDS + j;
 #pragma unroll
     for (int q = 0; q < Q; ++q) {
-      const int k = (j + q * T) & ((1 << logNs) - 1);
       float2 w[LAST];
 #pragma unroll
       for (int m = 0; m < LAST; ++m) {
         w[m] = v[q + m * Q];
-        if (m > 0) w[m] = cmul(w[m], twiddle<SIGN>(tw, m * k, C::LOG_L));
+        if (m > 0) w[m] = cmul(w[m], stw<SIGN>(wl + (q * (LAST - 1) + (m - 1)) * T));
       }
       dft_reg<LAST, SIGN>(w);
 #pragma unroll
