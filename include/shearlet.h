@@ -154,6 +154,35 @@ shl_status shl_decompose(const shl_bank* bank, const float* x, int batch, void* 
                          shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream);
 
 /*
+ * shl_decompose_noalloc - shl_decompose without a caller-provided workspace
+ * (the paper has no counterpart; this is a deployment convenience).
+ * For callers that cannot allocate device memory when they call: a host
+ * framework that owns all device memory and offers plug-ins no allocator, a
+ * latency-critical loop that cannot afford cudaMalloc's implicit device
+ * synchronisation, or a service at its memory budget that must not fail
+ * with out-of-memory at call time.
+ *   Scratch: a fixed array of SHL_NOALLOC_SCRATCH_BYTES compiled into the
+ *   library, which every GPU that loads the library holds until the process
+ *   exits.  The call allocates nothing (no cudaMalloc or cudaFree).
+ *   Limit: the image spectra of the batch plus one subband plane must fit,
+ *   (batch + 1) * rows * (cols/2 + 1) * 8 bytes <= SHL_NOALLOC_SCRATCH_BYTES
+ *   (e.g. batch <= 30 at 512 x 512); larger batches return SHL_EINVAL with a
+ *   message - use shl_decompose with your own workspace instead.
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before capturing any stream work that uses this entry point.
+ *   Sharing: all calls on a device share the one array, and it keeps whatever
+ *   the last call left there (nothing needs to start at zero).  Calls whose
+ *   kernels overlap on the GPU - on different streams, or from different
+ *   threads without ordering - race on it and give wrong results; order them
+ *   on one stream.
+ * Other arguments and the result are exactly those of shl_decompose.
+ */
+#define SHL_NOALLOC_SCRATCH_BYTES (32u << 20)
+shl_status shl_decompose_noalloc(const shl_bank* bank, const float* x, int batch, void* coeffs,
+                                 shl_dtype dtype, int flags, void* stream);
+
+/*
  * shl_decompose_masked - decomposition of u = mask * (f_masked - f_est) +
  * f_est, the input of one step of the inpainting iteration (Sec. 4.3, Alg.
  * "Shearlet inpainting by iterative hard thresholding"), with u formed while

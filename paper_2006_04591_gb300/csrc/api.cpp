@@ -188,8 +188,17 @@ shl_status check_common(const shl_bank* b, int batch, const void* ws, size_t ws_
 
 shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
                           const unsigned char* mask, const float* fest, int batch, void* coeffs,
-                          shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream) {
-  shl_status s = check_common(b, batch, ws, ws_bytes, SHL_OP_DECOMPOSE);
+                          shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream,
+                          int stage_override = 0) {
+  shl_status s;
+  if (stage_override <= 0) {
+    s = check_common(b, batch, ws, ws_bytes, SHL_OP_DECOMPOSE);
+  } else {
+    s = check_common(b, batch, ws, SIZE_MAX, SHL_OP_DECOMPOSE);
+    if (s == SHL_OK && batch > 0 &&
+        ws_bytes < align256((size_t)batch * plane_bytes(b)) + (size_t)stage_override * plane_bytes(b))
+      s = fail(SHL_EINVAL, "workspace too small for the requested staging depth");
+  }
   if (s != SHL_OK || batch == 0) return s;
   if (!x || !coeffs || !aligned16(x) || !aligned16(coeffs))
     return fail(SHL_EINVAL, "x and coeffs must be 16-byte aligned device pointers");
@@ -214,7 +223,7 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
     e = shl::launch_lines_fwd(N, X, batch * Mh, b->dTw, st);
   }
   if (e) return cuda_fail(e, "lines_fwd_image");
-  const int total = batch * K, S = stage_subbands(b);
+  const int total = batch * K, S = stage_override > 0 ? stage_override : stage_subbands(b);
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
   const float scale = (float)(1.0 / (double(N) * M));
   for (int s0 = 0; s0 < total; s0 += S) {
@@ -293,6 +302,24 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
 }
 
 }  // namespace
+
+namespace shl {
+shl_status set_error(shl_status s, const char* msg) { return fail(s, msg); }
+
+shl_status bank_geometry(const shl_bank* b, int* device, size_t* plane) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  *device = b->device;
+  *plane = plane_bytes(b);
+  return SHL_OK;
+}
+
+shl_status decompose_staged(const shl_bank* b, const float* x, int batch, void* coeffs,
+                            shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream,
+                            int stage_subbands_max) {
+  return decompose_impl(b, IN_F32, x, nullptr, nullptr, batch, coeffs, dtype, flags, ws, ws_bytes,
+                        stream, stage_subbands_max);
+}
+}  // namespace shl
 
 extern "C" {
 

@@ -7,6 +7,8 @@
 
 #include <vector>
 
+#include "../../include/shearlet.h"
+
 namespace shl {
 
 constexpr int TW_P = 4096;      // twiddle table length: exp(-2 pi i q / TW_P)
@@ -35,6 +37,15 @@ cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const floa
                              const float2* tw, cudaStream_t st);
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st);
+
+// Helpers of api.cpp used by noalloc.cu.
+shl_status set_error(shl_status s, const char* msg);
+shl_status bank_geometry(const shl_bank* b, int* device, size_t* plane_bytes);
+// shl_decompose with at most `stage_subbands_max` per-subband staging planes
+// after the batch's image spectra in ws.
+shl_status decompose_staged(const shl_bank* b, const float* x, int batch, void* coeffs,
+                            shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream,
+                            int stage_subbands_max);
 
 // Host float64 filter-bank construction (bank_build.cpp).
 struct HostBank {

@@ -60,6 +60,7 @@ def lib():
         "shl_workspace_size": (i, [vp, i, i, P(sz)]),
         "shl_decompose": (i, [vp, vp, i, vp, i, i, vp, sz, vp]),
         "shl_decompose_masked": (i, [vp, vp, vp, vp, i, vp, i, vp, sz, vp]),
+        "shl_decompose_noalloc": (i, [vp, vp, i, vp, i, i, vp]),
         "shl_reconstruct": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
         "shl_adjoint": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
         "shl_subband_absmax": (i, [vp, vp, i, i, i, vp, vp]),
@@ -169,6 +170,12 @@ def shl_decompose(h, x, batch, coeffs, dtype, flags, ws, stream=None):
     _check("shl_decompose", lib().shl_decompose(
         h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _ptr(ws), ws.numel() * ws.element_size(),
         _stream(stream, x.device)))
+
+
+def shl_decompose_noalloc(h, x, batch, coeffs, dtype, flags, stream=None):
+    """shl_decompose using the library's fixed scratch instead of a workspace."""
+    _check("shl_decompose_noalloc", lib().shl_decompose_noalloc(
+        h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _stream(stream, x.device)))
 
 
 def shl_decompose_masked(h, f_masked, mask, f_est, batch, coeffs, dtype, ws, stream=None):
