@@ -22,12 +22,12 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["fast.cu", "noalloc.cu"]
+CU_SOURCES = ["fast.cu", "noalloc.cu", "nn.cu"]
 CPP_SOURCES = ["api.cpp", "bank_build.cpp"]
 
 
 def _deps():
-    out = [os.path.join(ROOT, "include", "shearlet.h"), __file__]
+    out = [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))] + [__file__]
     for f in os.listdir(CSRC):
         out.append(os.path.join(CSRC, f))
     return out

@@ -1,0 +1,248 @@
+"""Learned per-subband thresholds for shearlet inpainting, and the
+coefficient-domain network step.
+
+Inpainting (Sec. 4.3, Alg. "Shearlet inpainting by iterative hard
+thresholding") runs T iterations of f <- SH^{-1} T_delta SH (M (f_m - f) + f)
+with thresholds delta_t RMS_i.  The plain method decays delta geometrically
+over 60 iterations.  Here a small CNN (ThresholdNet) looks at [f_masked, mask]
+and predicts all thresholds delta_{t,i} (t < 10, i < K) of a 10-iteration
+loop.  Training unrolls the 10 iterations with a relaxed threshold
+c sigmoid((|c| / delta - 1) / tau), tau annealed towards 0, and minimises the
+mean squared error to the clean image; its backward passes run through the
+adjoint transforms (shl_adjoint for the decomposition, the dual-weighted
+decomposition for the reconstruction) and the library's network kernels.
+Inference uses the hard threshold through shl_decompose_masked and
+shl_reconstruct, i.e. exactly the plain method's kernels with learned
+thresholds.  The plain loop stays as fallback and as the judge of PSNR.
+
+Run ``python -m paper_2006_04591_gb300.learned`` to train on 2,000 seeded
+512 x 512 pairs and compare with the plain method on 8 held-out images.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import queue
+import threading
+import time
+
+import numpy as np
+import torch
+
+from . import apps, nn, synth
+from .autograd import shearlet_dec, shearlet_rec
+from .shearlet import SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT, Bank
+
+
+def unrolled_iht(bank: Bank, f_masked, mask_u8, deltas, tau, rms):
+    """T relaxed iterations, differentiable in deltas [B, T, K] (x RMS_i)."""
+    f = torch.zeros_like(f_masked)
+    for t in range(deltas.shape[1]):
+        u = nn.mask_mix(f_masked, mask_u8, f)
+        c = shearlet_dec(u, bank)
+        f = shearlet_rec(nn.gate(c, deltas[:, t].contiguous(), tau, scale=rms), bank)
+    return f
+
+
+def hard_iht(bank: Bank, f_masked, mask_u8, thresholds, out_each=None):
+    """Hard-threshold iterations with given absolute thresholds [T, B, K]."""
+    B = f_masked.shape[0]
+    coeffs = torch.empty((B, bank.K, bank.rows, bank.cols), dtype=torch.float32,
+                         device=f_masked.device)
+    ws_d = bank.workspace(SHL_OP_DECOMPOSE, B)
+    ws_r = bank.workspace(SHL_OP_RECONSTRUCT, B)
+    f = torch.zeros_like(f_masked)
+    g = torch.empty_like(f)
+    for t in range(thresholds.shape[0]):
+        bank.decompose_masked(f_masked, mask_u8, f, out=coeffs, ws=ws_d)
+        bank.reconstruct(coeffs, thresh=thresholds[t], out=g, ws=ws_r)
+        f, g = g, f
+        if out_each is not None:
+            out_each(t, f)
+    return f
+
+
+def _softplus_inv(y):
+    return float(np.log(np.expm1(y)))
+
+
+def make_net(bank: Bank, T=10, delta0=5.0, delta_min=0.02, seed=0, pool=4, ch=32):
+    """ThresholdNet whose initial output is the plain geometric schedule."""
+    net = nn.ThresholdNet(bank.K, T=T, ch=ch, pool=pool, seed=seed, device="cuda:%d" % bank.device)
+    lam = (delta_min / delta0) ** (1.0 / max(T - 1, 1))
+    with torch.no_grad():
+        b = torch.tensor([_softplus_inv(delta0 * lam ** t) for t in range(T)], dtype=torch.float32)
+        net.bl.copy_(b.repeat_interleave(bank.K).to(net.bl.device))
+    return net
+
+
+class _Pairs:
+    """Background producer of seeded (clean, mask) pairs."""
+
+    def __init__(self, n, seed0, n_pairs, batch, p=0.5, rng_seed=0, depth=4):
+        self.q = queue.Queue(maxsize=depth)
+        self.stop = False
+        rng = np.random.default_rng(rng_seed)
+
+        def work():
+            while not self.stop:
+                seeds = seed0 + rng.integers(0, n_pairs, size=batch)
+                clean = np.stack([synth.cartoon_texture(n, n, int(s)) for s in seeds])
+                mask = np.stack([synth.bernoulli_mask(n, n, p, 50_000 + int(s)) for s in seeds])
+                self.q.put((clean.astype(np.float32), mask.astype(np.float32)))
+        self.th = threading.Thread(target=work, daemon=True)
+        self.th.start()
+
+    def get(self):
+        return self.q.get()
+
+    def close(self):
+        self.stop = True
+        try:
+            while True:
+                self.q.get_nowait()
+        except queue.Empty:
+            pass
+
+
+def train_thresholds(bank: Bank, steps=300, batch=4, T=10, n_pairs=2000, seed0=10000, lr=2e-3,
+                     tau0=0.3, tau1=0.02, delta0=5.0, log=None):
+    dev = torch.device("cuda", bank.device)
+    net = make_net(bank, T=T, delta0=delta0)
+    opt = nn.Adam(list(net.parameters()), lr=lr)
+    rms = torch.tensor(bank.rms, dtype=torch.float32, device=dev)
+    pairs = _Pairs(bank.rows, seed0, n_pairs, batch)
+    hist = []
+    try:
+        for step in range(steps):
+            tau = tau0 * (tau1 / tau0) ** (step / max(steps - 1, 1))
+            clean, mask = pairs.get()
+            fm = torch.from_numpy(clean * mask).to(dev)
+            clean = torch.from_numpy(clean).to(dev)
+            mu8 = torch.from_numpy(mask.astype(np.uint8)).to(dev)
+            mask = torch.from_numpy(mask).to(dev)
+            d = net(torch.stack([fm, mask], dim=1))
+            f = unrolled_iht(bank, fm, mu8, d, tau, rms)
+            loss = nn.mse(f, clean)
+            opt.zero_grad()
+            loss.backward()
+            opt.step()
+            if step % 25 == 0 or step == steps - 1:
+                l = float(loss.item())
+                hist.append((step, tau, l))
+                if log:
+                    log("step %d tau %.3f loss %.5f psnr %.2f" % (step, tau, l, -10 * math.log10(l)))
+    finally:
+        pairs.close()
+    return net, hist
+
+
+@torch.no_grad()
+def learned_thresholds(bank: Bank, net, fm, mask):
+    """Absolute thresholds [T, B, K] predicted by the network."""
+    d = net(torch.stack([fm, mask], dim=1))                       # [B, T, K]
+    rms = torch.tensor(bank.rms, dtype=torch.float32, device=fm.device)
+    th = torch.empty((d.shape[1], d.shape[0], d.shape[2]), dtype=torch.float32, device=fm.device)
+    nn.scale_thresholds(d, rms, th)
+    return th
+
+
+@torch.no_grad()
+def evaluate(bank: Bank, net, B=8, seed0=2000, plain_iters=60, delta_min=0.02, repeats=3):
+    """Plain 60-iteration IHT vs the learned 10-iteration loop on held-out images."""
+    dev = torch.device("cuda", bank.device)
+    clean, mask, masked = synth.inpaint_batch(B, bank.rows, 0.5, seed0)
+    clean_t = torch.from_numpy(clean.astype(np.float32)).to(dev)
+    fm = torch.from_numpy(masked.astype(np.float32)).to(dev)
+    mk = torch.from_numpy(mask.astype(np.float32)).to(dev)
+    mu8 = mk.to(torch.uint8)
+    rms = np.asarray(bank.rms, np.float64)
+    stream = torch.cuda.current_stream(dev)
+
+    def plain_thresholds():
+        d0 = apps.iht_start_threshold(bank, fm).double().cpu().numpy()
+        lam = (delta_min / d0) ** (1.0 / (plain_iters - 1))
+        deltas = d0[None, :] * lam[None, :] ** np.arange(plain_iters)[:, None]
+        return torch.from_numpy((deltas[:, :, None] * rms[None, None, :]).astype(np.float32)).to(dev)
+
+    # plain method: per-iteration PSNR (untimed pass) and per-iteration time (timed pass)
+    psnr_plain = []
+    hard_iht(bank, fm, mu8, plain_thresholds(),
+             out_each=lambda t, f: psnr_plain.append(apps.psnr(f, clean_t).mean().item()))
+    t_plain = []
+    for _ in range(repeats):
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(plain_iters + 1)]
+        torch.cuda.synchronize()
+        evs[0].record(stream)
+        th = plain_thresholds()          # includes the start-threshold pass and its host read
+        hard_iht(bank, fm, mu8, th, out_each=lambda t, f: evs[t + 1].record(stream))
+        torch.cuda.synchronize()
+        t_plain.append([evs[0].elapsed_time(e) / 1e3 for e in evs[1:]])
+    t_plain = np.median(np.asarray(t_plain), axis=0)
+
+    # learned: network + T hard iterations
+    f = hard_iht(bank, fm, mu8, learned_thresholds(bank, net, fm, mk))
+    p_learned = apps.psnr(f, clean_t).mean().item()
+    t_learned = []
+    for _ in range(repeats):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        hard_iht(bank, fm, mu8, learned_thresholds(bank, net, fm, mk))
+        b.record(stream)
+        torch.cuda.synchronize()
+        t_learned.append(a.elapsed_time(b) / 1e3)
+    t_learned = float(np.median(t_learned))
+    reach = [i for i, p in enumerate(psnr_plain) if p >= p_learned]
+    return {
+        "images": B, "size": bank.rows, "filters": bank.K, "mask": "Bernoulli(0.5)",
+        "plain_iterations": plain_iters, "plain_psnr_final": psnr_plain[-1],
+        "plain_seconds_total": float(t_plain[-1]),
+        "plain_psnr_per_iteration": psnr_plain,
+        "learned_iterations": int(net.T), "learned_psnr": p_learned,
+        "learned_seconds": t_learned,
+        "plain_seconds_to_learned_psnr": float(t_plain[reach[0]]) if reach else None,
+        "plain_iterations_to_learned_psnr": (reach[0] + 1) if reach else None,
+        "masked_psnr": apps.psnr(fm, clean_t).mean().item(),
+    }
+
+
+def coeff_net_step(bank: Bank, net, opt, x_noisy, clean):
+    """One training step of the coefficient-domain network: bfloat16
+    decomposition -> c + CNN(c) -> reconstruction -> MSE to the clean batch."""
+    c16 = shearlet_dec(x_noisy, bank, torch.bfloat16)
+    c = nn.bf16_to_float(c16)
+    y = shearlet_rec(net(c), bank)
+    loss = nn.mse(y, clean)
+    opt.zero_grad()
+    loss.backward()
+    opt.step()
+    return loss
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--size", type=int, default=512)
+    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    from . import _build
+    _build.build()
+    bank = Bank.create(args.size, args.size, 4, device=0)
+    t0 = time.time()
+    net, hist = train_thresholds(bank, steps=args.steps, batch=args.batch, log=print)
+    train_s = time.time() - t0
+    res = evaluate(bank, net)
+    res.update({"train_steps": args.steps, "train_batch": args.batch, "train_pairs": 2000,
+                "train_seconds": train_s, "train_history": hist})
+    print(json.dumps({k: v for k, v in res.items() if k != "plain_psnr_per_iteration"}))
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(res, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

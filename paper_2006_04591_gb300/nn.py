@@ -1,0 +1,421 @@
+"""Learned parts on the GPU: binding of include/shearlet_nn.h, autograd
+Functions whose forward and backward run in libshearlet's kernels, the two
+networks and Adam.
+
+* ThresholdNet - predicts per-subband thresholds delta_{t,i} (t < T, i < K)
+  of the unrolled inpainting iteration (Sec. 4.3) from [f_masked, mask]:
+  avgpool -> 4 x (3x3 conv + PReLU) -> global average pool -> linear ->
+  softplus.
+* CoeffNet - residual 3-layer CNN on shearlet coefficients after the learned
+  proximal operators of Sec. 4.4: c + W3 A W2 A W1 c, PReLU A.
+
+torch only provides tensors (memory), parameter containers and the autograd
+tape; every arithmetic step calls the library.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import math
+
+import torch
+
+from . import shearlet as S
+
+_sig_done = False
+
+
+def lib():
+    global _sig_done
+    L = S.lib()
+    if not _sig_done:
+        vp, i, f, ll, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_float, ctypes.c_longlong, ctypes.c_size_t
+        sig = {
+            "shl_nn_last_error": (ctypes.c_char_p, []),
+            "shl_nn_conv3x3_forward": (i, [vp, vp, vp, vp, i, i, i, i, i, vp]),
+            "shl_nn_conv3x3_workspace_floats": (sz, [i, i, i, i, i]),
+            "shl_nn_conv3x3_backward_data": (i, [vp, vp, vp, i, i, i, i, i, vp, vp]),
+            "shl_nn_conv3x3_backward_weight": (i, [vp, vp, vp, vp, i, i, i, i, i, vp, vp]),
+            "shl_nn_prelu_forward": (i, [vp, vp, vp, ll, vp]),
+            "shl_nn_reduce_workspace_floats": (sz, [ll]),
+            "shl_nn_prelu_backward": (i, [vp, vp, vp, vp, vp, ll, vp, vp]),
+            "shl_nn_avgpool": (i, [vp, vp, i, i, i, i, i, vp]),
+            "shl_nn_gap_forward": (i, [vp, vp, i, i, i, vp]),
+            "shl_nn_gap_backward": (i, [vp, vp, i, i, i, vp]),
+            "shl_nn_linear_forward": (i, [vp, vp, vp, vp, i, i, i, vp]),
+            "shl_nn_linear_backward": (i, [vp, vp, vp, vp, vp, vp, i, i, i, vp]),
+            "shl_nn_softplus_forward": (i, [vp, vp, ll, vp]),
+            "shl_nn_softplus_backward": (i, [vp, vp, vp, ll, vp]),
+            "shl_nn_gate_forward": (i, [vp, i, vp, vp, i, f, vp, i, ll, vp]),
+            "shl_nn_gate_workspace_floats": (sz, [i]),
+            "shl_nn_gate_backward": (i, [vp, vp, vp, i, f, vp, vp, vp, i, ll, vp, vp]),
+            "shl_nn_mse_forward": (i, [vp, vp, vp, ll, vp, vp]),
+            "shl_nn_mse_backward": (i, [vp, vp, vp, vp, ll, vp]),
+            "shl_nn_adam": (i, [vp, vp, vp, vp, ll, f, f, f, f, i, vp]),
+            "shl_nn_mask_mix": (i, [vp, vp, vp, vp, ll, vp]),
+            "shl_nn_mask_mix_backward": (i, [vp, vp, vp, ll, vp]),
+            "shl_nn_cast": (i, [vp, i, vp, ll, vp]),
+            "shl_nn_axpy": (i, [vp, f, vp, ll, vp]),
+            "shl_nn_scale_thresholds": (i, [vp, vp, vp, i, i, i, vp]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _sig_done = True
+    return L
+
+
+def _chk(name, st):
+    if st != 0:
+        raise S.ShearletError(name, st, lib().shl_nn_last_error().decode())
+
+
+def _p(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _st(t):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ws(n, like):
+    return torch.empty(max(int(n), 1), dtype=torch.float32, device=like.device)
+
+
+# ----------------------------------------------------------- C-named calls
+def shl_nn_conv3x3_forward(x, w, b, out):
+    B, Ci, H, W = x.shape
+    _chk("conv3x3_forward", lib().shl_nn_conv3x3_forward(_p(x), _p(w), _p(b), _p(out), B, Ci,
+                                                          w.shape[0], H, W, _st(x)))
+
+
+def shl_nn_conv3x3_backward(x, w, gout, need_gin=True):
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    L = lib()
+    ws = _ws(L.shl_nn_conv3x3_workspace_floats(B, Ci, Co, H, W), x)
+    gw = torch.empty_like(w)
+    gb = torch.empty(Co, dtype=torch.float32, device=x.device)
+    _chk("conv3x3_backward_weight", L.shl_nn_conv3x3_backward_weight(
+        _p(x), _p(gout), _p(gw), _p(gb), B, Ci, Co, H, W, _p(ws), _st(x)))
+    gin = None
+    if need_gin:
+        gin = torch.empty_like(x)
+        _chk("conv3x3_backward_data", L.shl_nn_conv3x3_backward_data(
+            _p(gout), _p(w), _p(gin), B, Ci, Co, H, W, _p(ws), _st(x)))
+    return gin, gw, gb
+
+
+# ------------------------------------------------------------- autograd
+class _Conv3x3(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, w, b):
+        x = x.contiguous()
+        out = torch.empty((x.shape[0], w.shape[0], x.shape[2], x.shape[3]), dtype=torch.float32,
+                          device=x.device)
+        shl_nn_conv3x3_forward(x, w.contiguous(), b.contiguous(), out)
+        ctx.save_for_backward(x, w)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        x, w = ctx.saved_tensors
+        gin, gw, gb = shl_nn_conv3x3_backward(x, w.contiguous(), gout.contiguous(),
+                                             ctx.needs_input_grad[0])
+        return gin, gw, gb
+
+
+class _PReLU(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, a):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        _chk("prelu_forward", lib().shl_nn_prelu_forward(_p(x), _p(a), _p(y), x.numel(), _st(x)))
+        ctx.save_for_backward(x, a)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, a = ctx.saved_tensors
+        gx = torch.empty_like(x)
+        ga = torch.empty(1, dtype=torch.float32, device=x.device)
+        ws = _ws(lib().shl_nn_reduce_workspace_floats(x.numel()), x)
+        _chk("prelu_backward", lib().shl_nn_prelu_backward(_p(x), _p(a), _p(gy.contiguous()), _p(gx),
+                                                            _p(ga), x.numel(), _p(ws), _st(x)))
+        return gx, ga.reshape(a.shape)
+
+
+class _GAP(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        B, C, H, W = x.shape
+        y = torch.empty((B, C), dtype=torch.float32, device=x.device)
+        _chk("gap_forward", lib().shl_nn_gap_forward(_p(x.contiguous()), _p(y), B, C, H * W, _st(x)))
+        ctx.shape = x.shape
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        B, C, H, W = ctx.shape
+        gx = torch.empty(ctx.shape, dtype=torch.float32, device=gy.device)
+        _chk("gap_backward", lib().shl_nn_gap_backward(_p(gy.contiguous()), _p(gx), B, C, H * W, _st(gy)))
+        return gx
+
+
+class _Linear(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, w, b):
+        B, I = x.shape
+        O = w.shape[0]
+        y = torch.empty((B, O), dtype=torch.float32, device=x.device)
+        _chk("linear_forward", lib().shl_nn_linear_forward(_p(x.contiguous()), _p(w), _p(b), _p(y), B, I, O, _st(x)))
+        ctx.save_for_backward(x, w)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        x, w = ctx.saved_tensors
+        B, I = x.shape
+        O = w.shape[0]
+        gx = torch.empty_like(x)
+        gw = torch.empty_like(w)
+        gb = torch.empty(O, dtype=torch.float32, device=x.device)
+        _chk("linear_backward", lib().shl_nn_linear_backward(_p(x.contiguous()), _p(w), _p(gy.contiguous()), _p(gx),
+                                                              _p(gw), _p(gb), B, I, O, _st(x)))
+        return gx, gw, gb
+
+
+class _Softplus(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        x = x.contiguous()
+        y = torch.empty_like(x)
+        _chk("softplus_forward", lib().shl_nn_softplus_forward(_p(x), _p(y), x.numel(), _st(x)))
+        ctx.save_for_backward(x)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        (x,) = ctx.saved_tensors
+        gx = torch.empty_like(x)
+        _chk("softplus_backward", lib().shl_nn_softplus_backward(_p(x), _p(gy.contiguous()), _p(gx), x.numel(), _st(x)))
+        return gx
+
+
+class _Gate(torch.autograd.Function):
+    """Relaxed hard threshold on [B, K, H, W] float32 coefficients with
+    thresholds delta [B, K] (times scale [K] if given)."""
+
+    @staticmethod
+    def forward(ctx, c, delta, scale, tau):
+        assert c.dtype == torch.float32, "gate takes float32 coefficients"
+        c = c.contiguous()
+        delta = delta.contiguous()
+        B, K, H, W = c.shape
+        y = torch.empty(c.shape, dtype=torch.float32, device=c.device)
+        _chk("gate_forward", lib().shl_nn_gate_forward(_p(c), 0, _p(delta), _p(scale), K,
+                                                        float(tau), _p(y), B * K, H * W, _st(c)))
+        ctx.save_for_backward(c, delta)
+        ctx.scale = scale
+        ctx.tau = float(tau)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        c, delta = ctx.saved_tensors
+        B, K, H, W = c.shape
+        gc = torch.empty_like(c)
+        gd = torch.empty_like(delta)
+        ws = _ws(lib().shl_nn_gate_workspace_floats(B * K), c)
+        _chk("gate_backward", lib().shl_nn_gate_backward(_p(c), _p(delta), _p(ctx.scale), K, ctx.tau,
+                                                          _p(gy.contiguous()), _p(gc), _p(gd), B * K,
+                                                          H * W, _p(ws), _st(c)))
+        return gc, gd, None, None
+
+
+class _MaskMix(torch.autograd.Function):
+    """u = mask (f_masked - f) + f, differentiable in f."""
+
+    @staticmethod
+    def forward(ctx, f_masked, mask_u8, f):
+        u = torch.empty_like(f)
+        _chk("mask_mix", lib().shl_nn_mask_mix(_p(f_masked.contiguous()), _p(mask_u8), _p(f.contiguous()), _p(u),
+                                                f.numel(), _st(f)))
+        ctx.save_for_backward(mask_u8)
+        return u
+
+    @staticmethod
+    def backward(ctx, gu):
+        (mask_u8,) = ctx.saved_tensors
+        gf = torch.empty_like(gu)
+        _chk("mask_mix_backward", lib().shl_nn_mask_mix_backward(_p(mask_u8), _p(gu.contiguous()), _p(gf),
+                                                                  gu.numel(), _st(gu)))
+        return None, None, gf
+
+
+class _MSE(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, a, b):
+        a, b = a.contiguous(), b.contiguous()
+        out = torch.empty(1, dtype=torch.float32, device=a.device)
+        ws = _ws(lib().shl_nn_reduce_workspace_floats(a.numel()), a)
+        _chk("mse_forward", lib().shl_nn_mse_forward(_p(a), _p(b), _p(out), a.numel(), _p(ws), _st(a)))
+        ctx.save_for_backward(a, b)
+        return (out / a.numel()).reshape(())
+
+    @staticmethod
+    def backward(ctx, g):
+        a, b = ctx.saved_tensors
+        ga = torch.empty_like(a)
+        gs = g.reshape(1).contiguous().float()
+        _chk("mse_backward", lib().shl_nn_mse_backward(_p(a), _p(b), _p(gs), _p(ga), a.numel(), _st(a)))
+        return ga, None
+
+
+def conv3x3(x, w, b):
+    return _Conv3x3.apply(x, w, b)
+
+
+def prelu(x, a):
+    return _PReLU.apply(x, a)
+
+
+def gap(x):
+    return _GAP.apply(x)
+
+
+def linear(x, w, b):
+    return _Linear.apply(x, w, b)
+
+
+def softplus(x):
+    return _Softplus.apply(x)
+
+
+def gate(c, delta, tau, scale=None):
+    return _Gate.apply(c, delta, scale, tau)
+
+
+def mask_mix(f_masked, mask_u8, f):
+    return _MaskMix.apply(f_masked, mask_u8, f)
+
+
+def mse(a, b):
+    return _MSE.apply(a, b)
+
+
+def scale_thresholds(d, scale, out):
+    """out[t][b][k] = d[b][t][k] * scale[k] (no grad)."""
+    B, T, K = d.shape
+    _chk("scale_thresholds", lib().shl_nn_scale_thresholds(_p(d.contiguous()), _p(scale), _p(out), B, T, K, _st(d)))
+    return out
+
+
+def avgpool(x, f):
+    B, C, H, W = x.shape
+    y = torch.empty((B, C, H // f, W // f), dtype=torch.float32, device=x.device)
+    _chk("avgpool", lib().shl_nn_avgpool(_p(x.contiguous()), _p(y), B, C, H, W, f, _st(x)))
+    return y
+
+
+def to_float(c):
+    """bfloat16 -> float32 through the library's cast kernel (no grad)."""
+    y = torch.empty(c.shape, dtype=torch.float32, device=c.device)
+    _chk("cast", lib().shl_nn_cast(_p(c.contiguous()), 1, _p(y), c.numel(), _st(c)))
+    return y
+
+
+class _ToFloat(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, c):
+        return to_float(c)
+
+    @staticmethod
+    def backward(ctx, g):
+        y = torch.empty(g.shape, dtype=torch.bfloat16, device=g.device)
+        _chk("cast", lib().shl_nn_cast(_p(g.contiguous()), 0, _p(y), g.numel(), _st(g)))
+        return y
+
+
+def bf16_to_float(c):
+    return _ToFloat.apply(c)
+
+
+# ---------------------------------------------------------------- models
+def _init_conv(co, ci, gen, device):
+    std = math.sqrt(2.0 / (ci * 9))
+    w = torch.randn((co, ci, 3, 3), generator=gen) * std
+    return w.to(device).requires_grad_(True), torch.zeros(co, device=device, requires_grad=True)
+
+
+class ThresholdNet(torch.nn.Module):
+    """[B, 2, H, W] (f_masked, mask) -> thresholds [B, T, K] (relative to RMS_i)."""
+
+    def __init__(self, K, T=10, ch=32, pool=4, seed=0, device="cuda", scale=1.0):
+        super().__init__()
+        g = torch.Generator().manual_seed(seed)
+        self.K, self.T, self.pool = K, T, pool
+        chans = [2, ch, ch, ch, ch]
+        for l in range(4):
+            w, b = _init_conv(chans[l + 1], chans[l], g, device)
+            setattr(self, "w%d" % l, torch.nn.Parameter(w.detach()))
+            setattr(self, "b%d" % l, torch.nn.Parameter(b.detach()))
+            setattr(self, "a%d" % l, torch.nn.Parameter(torch.full((1,), 0.25, device=device)))
+        self.wl = torch.nn.Parameter((torch.randn((T * K, ch), generator=g) * 0.01).to(device))
+        self.bl = torch.nn.Parameter(torch.full((T * K,), float(scale), device=device))
+
+    def forward(self, x):
+        h = avgpool(x, self.pool) if self.pool > 1 else x
+        for l in range(4):
+            h = prelu(conv3x3(h, getattr(self, "w%d" % l), getattr(self, "b%d" % l)),
+                      getattr(self, "a%d" % l))
+        y = softplus(linear(gap(h), self.wl, self.bl))
+        return y.reshape(x.shape[0], self.T, self.K)
+
+
+class CoeffNet(torch.nn.Module):
+    """c + W3 A W2 A W1 c on [B, K, H, W] float32 coefficients."""
+
+    def __init__(self, K, ch=32, seed=0, device="cuda"):
+        super().__init__()
+        g = torch.Generator().manual_seed(seed)
+        chans = [K, ch, ch, K]
+        for l in range(3):
+            w, b = _init_conv(chans[l + 1], chans[l], g, device)
+            if l == 2:
+                w = w * 0.1
+            setattr(self, "w%d" % l, torch.nn.Parameter(w.detach()))
+            setattr(self, "b%d" % l, torch.nn.Parameter(b.detach()))
+        self.a0 = torch.nn.Parameter(torch.full((1,), 0.25, device=device))
+        self.a1 = torch.nn.Parameter(torch.full((1,), 0.25, device=device))
+
+    def forward(self, c):
+        h = prelu(conv3x3(c, self.w0, self.b0), self.a0)
+        h = prelu(conv3x3(h, self.w1, self.b1), self.a1)
+        return c + conv3x3(h, self.w2, self.b2)
+
+
+class Adam:
+    """Adam over a list of parameters; the update runs in shl_nn_adam."""
+
+    def __init__(self, params, lr=1e-3, betas=(0.9, 0.999), eps=1e-8):
+        self.params = [p for p in params]
+        self.lr, self.b1, self.b2, self.eps = lr, betas[0], betas[1], eps
+        self.m = [torch.zeros_like(p) for p in self.params]
+        self.v = [torch.zeros_like(p) for p in self.params]
+        self.step_count = 0
+
+    def zero_grad(self):
+        for p in self.params:
+            p.grad = None
+
+    @torch.no_grad()
+    def step(self):
+        self.step_count += 1
+        for p, m, v in zip(self.params, self.m, self.v):
+            if p.grad is None:
+                continue
+            _chk("adam", lib().shl_nn_adam(_p(p), _p(p.grad.contiguous()), _p(m), _p(v), p.numel(),
+                                            self.lr, self.b1, self.b2, self.eps, self.step_count,
+                                            _st(p)))

@@ -78,9 +78,14 @@ def lib():
 
 
 def header_symbols() -> list[str]:
-    """Function names declared in include/shearlet.h."""
-    txt = open(HEADER).read()
-    return sorted(set(re.findall(r"^[A-Za-z_][\w \*]*?\b(shl_\w+)\s*\(", txt, re.M)))
+    """Function names declared in include/*.h."""
+    inc = os.path.dirname(HEADER)
+    names = set()
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            txt = open(os.path.join(inc, h)).read()
+            names |= set(re.findall(r"^[A-Za-z_][\w \*]*?\b(shl_\w+)\s*\(", txt, re.M))
+    return sorted(names)
 
 
 def _check(fn, status):

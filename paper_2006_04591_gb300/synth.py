@@ -34,6 +34,13 @@ def _coords(n: int, m: int):
     return y.astype(np.float64), x.astype(np.float64)
 
 
+def _box(n, m, cy, cx, r):
+    """Index ranges of the grid points within distance r of (cy, cx)."""
+    y0, y1 = max(0, int(np.floor(cy - r)) - 1), min(n, int(np.ceil(cy + r)) + 2)
+    x0, x1 = max(0, int(np.floor(cx - r)) - 1), min(m, int(np.ceil(cx + r)) + 2)
+    return slice(y0, y1), slice(x0, x1)
+
+
 def _paint_ellipse(img, rng, y, x):
     n, m = img.shape
     s = min(n, m)
@@ -41,10 +48,12 @@ def _paint_ellipse(img, rng, y, x):
     a, b = rng.uniform(s / 16, s / 4), rng.uniform(s / 16, s / 4)
     th = rng.uniform(0, np.pi)
     val = rng.uniform(0, 1)
-    dy, dx = y - cy, x - cx
+    sy, sx = _box(n, m, cy, cx, max(a, b))      # only points that can be inside
+    dy, dx = y[sy, sx] - cy, x[sy, sx] - cx
     u = dx * np.cos(th) + dy * np.sin(th)
     v = -dx * np.sin(th) + dy * np.cos(th)
-    img[(u / a) ** 2 + (v / b) ** 2 <= 1.0] = val
+    sub = img[sy, sx]
+    sub[(u / a) ** 2 + (v / b) ** 2 <= 1.0] = val
 
 
 def _paint_polygon(img, rng, y, x):
@@ -56,14 +65,17 @@ def _paint_polygon(img, rng, y, x):
     ang = np.sort(rng.uniform(0, 2 * np.pi, size=nv))
     val = rng.uniform(0, 1)
     vy, vx = cy + r * np.sin(ang), cx + r * np.cos(ang)
-    inside = np.ones(img.shape, dtype=bool)
+    sy, sx = _box(n, m, cy, cx, r)              # the polygon lies in its circle
+    yy, xx = y[sy, sx], x[sy, sx]
+    inside = np.ones(yy.shape, dtype=bool)
     for k in range(nv):
         y0, x0 = vy[k], vx[k]
         y1, x1 = vy[(k + 1) % nv], vx[(k + 1) % nv]
         # counter-clockwise vertices: interior on the left of each edge
-        cross = (x1 - x0) * (y - y0) - (y1 - y0) * (x - x0)
+        cross = (x1 - x0) * (yy - y0) - (y1 - y0) * (xx - x0)
         inside &= cross >= 0
-    img[inside] = val
+    sub = img[sy, sx]
+    sub[inside] = val
 
 
 def ellipses(n: int, m: int | None = None, count: int = 8, seed: int = 1):
