@@ -55,6 +55,27 @@ def _algorithmic_bytes(B, K, N, M, s=4):
     return dec, rec
 
 
+# ------------------------------------------------------- multi-rank logic
+def rank_seeds(rank: int, batch: int, base: int = 100):
+    """Image seeds of one replica: each rank decomposes its own batch."""
+    return [base + rank * batch + b for b in range(batch)]
+
+
+def reduce_max_time(t_local: float, dist, device) -> float:
+    """Max over ranks of a step time (the slowest replica bounds the job)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return t_local
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world: int, t_step: float) -> float:
+    """Whole-job throughput: units processed by all ranks / max step time."""
+    return units_per_rank * world / t_step
+
+
 # ----------------------------------------------------------------- clocks
 class ClockSampler:
     def __init__(self, device_index=0):
@@ -182,7 +203,7 @@ def run_gpu(args):
     bank = S.Bank.create(N_IMG, N_IMG, SCALES, device=local)
     assert bank.K == K_FILT
     B, N, K = B_IMG, N_IMG, K_FILT
-    x_host = np.stack([synth.cartoon(N, N, 100 + rank * B + b) for b in range(B)]).astype(np.float32)
+    x_host = np.stack([synth.cartoon(N, N, sd) for sd in rank_seeds(rank, B)]).astype(np.float32)
     x = torch.from_numpy(x_host).to(dev)
     coeffs = torch.empty((B, K, N, N), dtype=torch.float32, device=dev)
     xr = torch.empty((B, N, N), dtype=torch.float32, device=dev)
@@ -220,11 +241,8 @@ def run_gpu(args):
     times = timed(step, args.steps)
     launches = S.shl_launch_count() - n0
     clock_info = clocks.stop()
-    t_step = sum(times) / len(times) / 1e3
+    t_step = reduce_max_time(sum(times) / len(times) / 1e3, dist if world > 1 else None, dev)
     if world > 1:
-        t = torch.tensor([t_step], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_step = t.item()
         dist.barrier()
 
     # per-kernel timing with CUDA events on the launch stream (separate pass)
@@ -252,7 +270,7 @@ def run_gpu(args):
     t_e2e = sum(e2e_times) / len(e2e_times) / 1e3
 
     coeffs_per_step = B * K * N * N * world
-    value = coeffs_per_step / t_step
+    value = job_value(B * K * N * N, world, t_step)
     dec_b, rec_b = _algorithmic_bytes(B, K, N, N)
     peaks = {}
     try:

@@ -132,8 +132,9 @@ shl_status shl_bank_copy_info(const shl_bank* bank, int* idx, double* rms, doubl
 /*
  * shl_workspace_size - bytes of device workspace ``op`` needs for ``batch``
  * images.  The workspace holds the image spectra (decompose) or the
- * per-image accumulators (reconstruct / adjoint) plus an L2-sized staging
- * area for per-subband intermediates.  Its contents on entry are ignored.
+ * per-image accumulators (reconstruct / adjoint) plus a staging area for
+ * per-subband intermediates (up to 1 GiB, e.g. all 784 subbands of 16
+ * images at 512 x 512 with 49 filters).  Its contents on entry are ignored.
  */
 shl_status shl_workspace_size(const shl_bank* bank, shl_op op, int batch, size_t* bytes);
 

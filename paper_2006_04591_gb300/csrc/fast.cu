@@ -200,18 +200,17 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
 
     // conjugate-pair split needs Z[L - k]: publish the natural-order line
     group_sync<T>(1 + r);
-#pragma unroll
-    for (int u = 0; u < R; ++u) line[pad_index(j + u * T, P::C::LOG_R)] = v[u];
+    line_store<L, R>(v, line, j);
     group_sync<T>(1 + r);
+    float2 mir[R];
+    line_load_mirror<L, R>(mir, line, j);
     const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], kept by lane j == 0
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const int kk = j + u * T;
-      const float2 A = v[u];
-      const float2 B = line[pad_index((L - kk) & (L - 1), P::C::LOG_R)];
+      const float2 A = v[u], B = mir[u];
       const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
       const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      v[u] = cadd(E, cmul(O, ptw[kk]));
+      v[u] = cadd(E, cmul(O, ptw[j + u * T]));
     }
     __syncthreads();                       // line buffers become the tile
     if (valid) {
@@ -220,10 +219,12 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
       if (j == 0) tile[L * TP + r] = nyq;
     }
     __syncthreads();
+    // transposed store: two rows of one kx per 16-byte store
     float2* out = a.out + (size_t)s * Mh * a.N + y0;
-    for (int idx = tid; idx < Mh * TR; idx += P::THREADS) {
-      const int kx = idx / TR, q = idx % TR;
-      out[(size_t)kx * a.N + q] = tile[kx * TP + q];
+    for (int idx = tid; idx < Mh * (TR / 2); idx += P::THREADS) {
+      const int kx = idx / (TR / 2), q = 2 * (idx % (TR / 2));
+      const float2 lo = tile[kx * TP + q], hi = tile[kx * TP + q + 1];
+      *reinterpret_cast<float4*>(out + (size_t)kx * a.N + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
     }
     __syncthreads();                       // tile / stage reuse
   }

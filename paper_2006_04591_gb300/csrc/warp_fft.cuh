@@ -99,12 +99,19 @@ __device__ __forceinline__ float2 stw(const float2* p) {
 // X[j + u*T].  SIGN = -1 forward, +1 inverse (unnormalised).  sm is the
 // group's padded line buffer (LineCfg::WORDS float2); stw_sm holds the
 // staged twiddles of LineTw<L, R>.
+// Padded position of element p + u * stride when the base p is fixed per lane
+// and stride is a multiple of R: pad(p) + u * (stride + stride / R).
+template <int R>
+__device__ __forceinline__ int pad_base(int p) { return p + (p >> ilog2(R)); }
+
 template <int L, int R, int SIGN>
 __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int bar_id,
                                          const float2* __restrict__ stw_sm) {
   using C = LineCfg<L, R>;
   using W = LineTw<L, R>;
   constexpr int T = C::T;
+  constexpr bool T_ALIGNED = (T % R) == 0;         // read stride is a multiple of R
+  const int rbase = pad_base<R>(j);
 #pragma unroll
   for (int st = 0; st < C::NFULL; ++st) {
     const int logNs = st * C::LOG_R;
@@ -116,13 +123,27 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int 
     }
     dft_reg<R, SIGN>(v);
     if (st < C::NFULL - 1 || C::LAST > 1) {
-      const int idxD = ((j >> logNs) << (logNs + C::LOG_R)) + (j & (Ns - 1));
       group_sync<T>(bar_id);
+      if (st == 0) {
+        // positions j R + u: padded j (R + 1) + u
+        float2* wp = sm + j * (R + 1);
 #pragma unroll
-      for (int u = 0; u < R; ++u) sm[pad_index(idxD + u * Ns, C::LOG_R)] = v[u];
+        for (int u = 0; u < R; ++u) wp[u] = v[u];
+      } else {
+        const int idxD = ((j >> logNs) << (logNs + C::LOG_R)) + (j & (Ns - 1));
+        float2* wp = sm + pad_base<R>(idxD);
+#pragma unroll
+        for (int u = 0; u < R; ++u) wp[u * (Ns + Ns / R)] = v[u];
+      }
       group_sync<T>(bar_id);
+      if constexpr (T_ALIGNED) {
+        const float2* rp = sm + rbase;
 #pragma unroll
-      for (int u = 0; u < R; ++u) v[u] = sm[pad_index(j + u * T, C::LOG_R)];
+        for (int u = 0; u < R; ++u) v[u] = rp[u * (T + T / R)];
+      } else {
+#pragma unroll
+        for (int u = 0; u < R; ++u) v[u] = sm[pad_index(j + u * T, C::LOG_R)];
+      }
     }
   }
   if constexpr (C::LAST > 1) {
@@ -141,6 +162,40 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int 
 #pragma unroll
       for (int m = 0; m < LAST; ++m) v[q + m * Q] = w[m];
     }
+  }
+}
+
+// Store v[u] (natural positions j + u T) into the padded line buffer.
+template <int L, int R>
+__device__ __forceinline__ void line_store(const float2 (&v)[R], float2* sm, int j) {
+  constexpr int T = L / R;
+  if constexpr (T % R == 0) {
+    float2* p = sm + pad_base<R>(j);
+#pragma unroll
+    for (int u = 0; u < R; ++u) p[u * (T + T / R)] = v[u];
+  } else {
+#pragma unroll
+    for (int u = 0; u < R; ++u) sm[pad_index(j + u * T, ilog2(R))] = v[u];
+  }
+}
+
+// Load the mirrored elements X[(L - (j + u T)) mod L], u = 0..R-1, from the
+// padded line buffer (the conjugate-pair partners of the real-FFT split).
+template <int L, int R>
+__device__ __forceinline__ void line_load_mirror(float2 (&out)[R], const float2* sm, int j) {
+  constexpr int T = L / R;
+  if constexpr (T % R == 0) {
+    // j > 0: L - j - uT = (T - j) + (R - 1 - u) T;  j == 0: ((R - u) mod R) T
+    constexpr int S = T + T / R;
+    const float2* p = sm + (j > 0 ? pad_base<R>(T - j) : 0);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int off = j > 0 ? (R - 1 - u) * S : ((R - u) & (R - 1)) * S;
+      out[u] = p[off];
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < R; ++u) out[u] = sm[pad_index((L - (j + u * T)) & (L - 1), ilog2(R))];
   }
 }
 

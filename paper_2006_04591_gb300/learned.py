@@ -79,32 +79,54 @@ def make_net(bank: Bank, T=10, delta0=5.0, delta_min=0.02, seed=0, pool=4, ch=32
 
 
 class _Pairs:
-    """Background producer of seeded (clean, mask) pairs."""
+    """Seeded (clean, mask) batches produced ahead by worker threads.
 
-    def __init__(self, n, seed0, n_pairs, batch, p=0.5, rng_seed=0, depth=4):
-        self.q = queue.Queue(maxsize=depth)
-        self.stop = False
+    The seeds of every step are drawn up front, so the training data order is
+    deterministic; workers fill steps in a bounded window ahead of the
+    consumer."""
+
+    def __init__(self, n, seed0, n_pairs, batch, steps, p=0.5, rng_seed=0, workers=6, depth=12):
         rng = np.random.default_rng(rng_seed)
+        self.seeds = seed0 + rng.integers(0, n_pairs, size=(steps, batch))
+        self.n, self.p = n, p
+        self.ready = {}
+        self.next_get = 0
+        self.cv = threading.Condition()
+        self.stop = False
+        self.depth = depth
+        self.threads = [threading.Thread(target=self._work, args=(w, workers), daemon=True)
+                        for w in range(workers)]
+        for t in self.threads:
+            t.start()
 
-        def work():
-            while not self.stop:
-                seeds = seed0 + rng.integers(0, n_pairs, size=batch)
-                clean = np.stack([synth.cartoon_texture(n, n, int(s)) for s in seeds])
-                mask = np.stack([synth.bernoulli_mask(n, n, p, 50_000 + int(s)) for s in seeds])
-                self.q.put((clean.astype(np.float32), mask.astype(np.float32)))
-        self.th = threading.Thread(target=work, daemon=True)
-        self.th.start()
+    def _work(self, w, nw):
+        for k in range(w, len(self.seeds), nw):
+            with self.cv:
+                while not self.stop and k >= self.next_get + self.depth:
+                    self.cv.wait(timeout=1.0)
+                if self.stop:
+                    return
+            seeds = self.seeds[k]
+            clean = np.stack([synth.cartoon_texture(self.n, self.n, int(s)) for s in seeds])
+            mask = np.stack([synth.bernoulli_mask(self.n, self.n, self.p, 50_000 + int(s))
+                             for s in seeds])
+            with self.cv:
+                self.ready[k] = (clean.astype(np.float32), mask.astype(np.float32))
+                self.cv.notify_all()
 
     def get(self):
-        return self.q.get()
+        with self.cv:
+            while self.next_get not in self.ready:
+                self.cv.wait(timeout=1.0)
+            item = self.ready.pop(self.next_get)
+            self.next_get += 1
+            self.cv.notify_all()
+        return item
 
     def close(self):
-        self.stop = True
-        try:
-            while True:
-                self.q.get_nowait()
-        except queue.Empty:
-            pass
+        with self.cv:
+            self.stop = True
+            self.cv.notify_all()
 
 
 def train_thresholds(bank: Bank, steps=300, batch=4, T=10, n_pairs=2000, seed0=10000, lr=2e-3,
@@ -113,7 +135,7 @@ def train_thresholds(bank: Bank, steps=300, batch=4, T=10, n_pairs=2000, seed0=1
     net = make_net(bank, T=T, delta0=delta0)
     opt = nn.Adam(list(net.parameters()), lr=lr)
     rms = torch.tensor(bank.rms, dtype=torch.float32, device=dev)
-    pairs = _Pairs(bank.rows, seed0, n_pairs, batch)
+    pairs = _Pairs(bank.rows, seed0, n_pairs, batch, steps)
     hist = []
     try:
         for step in range(steps):
@@ -222,15 +244,51 @@ def coeff_net_step(bank: Bank, net, opt, x_noisy, clean):
     return loss
 
 
+def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3):
+    """Training-step time of the coefficient network (bfloat16 coefficients)."""
+    bank = Bank.create(N, N, scales, device=0)
+    dev = torch.device("cuda", 0)
+    clean, noisy = synth.denoise_batch(B, N, 30 / 255, seed0=1000)
+    x = torch.from_numpy(noisy.astype(np.float32)).to(dev)
+    y = torch.from_numpy(clean.astype(np.float32)).to(dev)
+    net = nn.CoeffNet(bank.K, ch=32, seed=0, device=dev)
+    opt = nn.Adam(list(net.parameters()), lr=1e-3)
+    losses = []
+    for _ in range(warmup):
+        losses.append(float(coeff_net_step(bank, net, opt, x, y).item()))
+    st = torch.cuda.current_stream(dev)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(st)
+    for _ in range(steps):
+        l = coeff_net_step(bank, net, opt, x, y)
+    b.record(st)
+    torch.cuda.synchronize()
+    losses.append(float(l.item()))
+    ms = a.elapsed_time(b) / steps
+    conv_flops = 2 * B * N * N * 9 * (bank.K * 32 + 32 * 32 + 32 * bank.K) * 3   # fwd + 2 bwd
+    return {"batch": B, "size": N, "filters": bank.K, "coeff_dtype": "bf16",
+            "ms_per_train_step": ms, "conv_tflops": conv_flops / (ms / 1e3) / 1e12,
+            "loss_first": losses[0], "loss_last": losses[-1]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--out", default=None)
+    ap.add_argument("--coeff-net", action="store_true", help="time the coefficient-network step")
     args = ap.parse_args()
     from . import _build
     _build.build()
+    if args.coeff_net:
+        res = time_coeff_net_step()
+        print(json.dumps(res))
+        if args.out:
+            with open(args.out, "w") as fh:
+                json.dump(res, fh, indent=1)
+        return
     bank = Bank.create(args.size, args.size, 4, device=0)
     t0 = time.time()
     net, hist = train_thresholds(bank, steps=args.steps, batch=args.batch, log=print)
