@@ -360,6 +360,11 @@ __global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
   }
 }
 
+// One lane group handles one kx line for DEC_FPG consecutive subbands of the
+// chunk: the image-spectrum line is loaded once per image and the next
+// filter's G line is fetched before the current FFT.
+constexpr int DEC_FPG = 4;
+
 template <int LOG_N>
 __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   using P = LinesT<LOG_N>;
@@ -370,24 +375,51 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   float2* twl = smem + (size_t)P::NG * P::C::WORDS;
   LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
   __syncthreads();
-  for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
-    const int sl = q / a.Mh, kx = q - sl * a.Mh;
-    const int s = a.s0 + sl;
-    const int b = s / a.K, i = s - b * a.K;
-    const float2* X = a.data + ((size_t)b * a.Mh + kx) * N;
-    const float* G = a.G + ((size_t)i * a.Mh + kx) * N;
+  const int S = a.nlines / a.Mh;                        // subbands in the chunk
+  const int ngroups = (S + DEC_FPG - 1) / DEC_FPG;
+  const int items = ngroups * a.Mh;
+  for (int q = blockIdx.x * P::NG + g; q < items; q += gridDim.x * P::NG) {
+    const int m = q / a.Mh, kx = q - m * a.Mh;
+    const int sl0 = m * DEC_FPG, sl1 = min(S, sl0 + DEC_FPG);
     const float* W = a.invW ? a.invW + (size_t)kx * N : nullptr;
-    float2 v[R];
+    float2 X[R];
+    float gn[R];
+    int b_loaded = -1;
+    {
+      const int s = a.s0 + sl0, b = s / a.K, i = s - b * a.K;
+      const float* G = a.G + ((size_t)i * a.Mh + kx) * N;
 #pragma unroll
-    for (int u = 0; u < R; ++u) {
-      float gv = __ldg(G + j + u * T) * a.scale;
-      if (W) gv *= __ldg(W + j + u * T);
-      v[u] = cscale(X[j + u * T], gv);
+      for (int u = 0; u < R; ++u) gn[u] = __ldg(G + j + u * T);
     }
-    line_fft<N, R, +1>(v, line, j, 1 + g, twl);
-    float2* out = a.out + (size_t)q * N;
+    for (int sl = sl0; sl < sl1; ++sl) {
+      const int s = a.s0 + sl, b = s / a.K;
+      if (b != b_loaded) {                              // image spectrum line, once per image
+        const float2* Xp = a.data + ((size_t)b * a.Mh + kx) * N;
 #pragma unroll
-    for (int u = 0; u < R; ++u) out[j + u * T] = v[u];
+        for (int u = 0; u < R; ++u) X[u] = Xp[j + u * T];
+        b_loaded = b;
+      }
+      float gc[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) gc[u] = gn[u];
+      if (sl + 1 < sl1) {                               // prefetch the next filter's line
+        const int s2 = s + 1, i2 = s2 - (s2 / a.K) * a.K;
+        const float* G2 = a.G + ((size_t)i2 * a.Mh + kx) * N;
+#pragma unroll
+        for (int u = 0; u < R; ++u) gn[u] = __ldg(G2 + j + u * T);
+      }
+      float2 v[R];
+#pragma unroll
+      for (int u = 0; u < R; ++u) {
+        float gv = gc[u] * a.scale;
+        if (W) gv *= __ldg(W + j + u * T);
+        v[u] = cscale(X[u], gv);
+      }
+      line_fft<N, R, +1>(v, line, j, 1 + g, twl);
+      float2* out = a.out + ((size_t)sl * a.Mh + kx) * N;
+#pragma unroll
+      for (int u = 0; u < R; ++u) out[j + u * T] = v[u];
+    }
   }
 }
 
@@ -525,7 +557,8 @@ static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra,
   cudaError_t e;
   if (mode == 0 || mode == 1) {
     if (a.nlines == 0) return cudaSuccess;
-    const int grid = std::min((a.nlines + P::NG - 1) / P::NG, sm_count() * 8);
+    const int work = mode == 1 ? ((a.nlines / a.Mh + DEC_FPG - 1) / DEC_FPG) * a.Mh : a.nlines;
+    const int grid = std::min((work + P::NG - 1) / P::NG, sm_count() * 8);
     const size_t sm = P::SMEM_LINES + P::TWB;
     if (mode == 0) {
       if ((e = prep(k_lines_fwd<LOG_N>, sm))) return e;

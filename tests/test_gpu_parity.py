@@ -219,3 +219,35 @@ def test_full_size_512_k49_sampled():
         want = OT.reconstruct(c[b].cpu().numpy().astype(np.float64), ref["psi_hat"]).real
         assert _rel(r[b].cpu().numpy(), want) <= TOL32
     assert (r - xt).abs().max().item() <= TOL32 * xt.abs().max().item()
+
+
+# ------------------------------------------------------------ rows of 512
+@pytest.mark.parametrize("rows,J,B", [(16, 1, 3), (256, 3, 2), (1024, 2, 1), (512, 2, 5)])
+def test_rows_of_512_decompose_f32_bf16_dual(rows, J, B):
+    """Rows of 512 (the benchmark's row length) with other column lengths and
+    batches of odd subband counts, in float32, bfloat16 and dual-weighted
+    form."""
+    ref, bank = _bank(rows, 512, J)
+    x = _images(B, rows, 512, 90)
+    xt = torch.from_numpy(x).cuda()
+    c32 = bank.decompose(xt).cpu().numpy()
+    c16 = bank.decompose(xt, dtype=torch.bfloat16).float().cpu().numpy()
+    cd = bank.decompose(xt, dual=True).cpu().numpy()
+    want, _ = OT.decompose_batch(x, ref["psi_hat"])
+    want_d, _ = OT.decompose_batch(x, ref["psi_hat"], dual=True)
+    for b in range(B):
+        assert _rel(c32[b], want[b]) <= TOL32, b
+        assert _rel(c16[b], want[b]) <= TOL16, b
+        assert _rel(cd[b], want_d[b]) <= TOL32, b
+
+
+def test_chunking_does_not_change_results():
+    """One staging chunk (the default) and many small chunks (the fixed
+    scratch of shl_decompose_noalloc) run the same arithmetic: equal bits."""
+    from paper_2006_04591_gb300 import shearlet as S
+    ref, bank = _bank(512, 512, 4)
+    x = torch.from_numpy(_images(4, 512, 512, 95)).cuda()
+    a = bank.decompose(x)
+    b = torch.empty_like(a)
+    S.shl_decompose_noalloc(bank.handle, x, 4, b, S.SHL_F32, 0)
+    assert torch.equal(a, b)
