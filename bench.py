@@ -55,6 +55,44 @@ def _algorithmic_bytes(B, K, N, M, s=4):
     return dec, rec
 
 
+# ------------------------------------------------- ncu traffic (profiles/)
+KERNEL_SOURCES = ("fast.cu", "warp_fft.cuh", "fft_core.cuh", "internal.h")
+
+
+def kernel_source_hash():
+    """First 16 hex digits of the SHA-256 of the transform kernels' sources;
+    the ncu summaries record it so that a stale figure is not reported."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2006_04591_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _profiled_traffic(kernel):
+    """DRAM bytes per subband of ``kernel`` from the committed ncu summary
+    profiles/<kernel>_512_k49.md, or None if it is absent or was taken on
+    other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "%s_512_k49.md" % kernel)
+    try:
+        lines = open(path).read().splitlines()
+        cur = kernel_source_hash()
+    except OSError:
+        return None
+    vals = {}
+    for line in lines:
+        key, sep, val = line.partition(":")
+        if sep:
+            vals[key.strip()] = val.strip()
+    if vals.get("source_sha256_16") != cur:
+        return None
+    try:
+        return float(vals["traffic_bytes_per_subband"])
+    except (KeyError, ValueError):
+        return None
+
+
 # ------------------------------------------------------- multi-rank logic
 def rank_seeds(rank: int, batch: int, base: int = 100):
     """Image seeds of one replica: each rank decomposes its own batch."""
@@ -235,12 +273,11 @@ def run_gpu(args):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local)     # sampled while the GPU runs the timed passes below
     clocks.start()
     n0 = S.shl_launch_count()
     times = timed(step, args.steps)
     launches = S.shl_launch_count() - n0
-    clock_info = clocks.stop()
     t_step = reduce_max_time(sum(times) / len(times) / 1e3, dist if world > 1 else None, dev)
     if world > 1:
         dist.barrier()
@@ -268,6 +305,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     e2e_times = timed(e2e_step, args.steps)
     t_e2e = sum(e2e_times) / len(e2e_times) / 1e3
+    clock_info = clocks.stop()
+    clock_info["window"] = "timed, per-kernel-event and end-to-end passes"
 
     coeffs_per_step = B * K * N * N * world
     value = job_value(B * K * N * N, world, t_step)
@@ -296,8 +335,10 @@ def run_gpu(args):
         step_bytes = per_kernel_bytes.get(name, 0)
         alg = step_bytes / per_step_launches if per_step_launches else 0
         achieved = alg / (per_launch_ms / 1e3) / 1e9
+        per_sub = _profiled_traffic(name)
+        traffic = per_sub * (B * K) / per_step_launches if per_sub is not None else None
         roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": None,
+                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
                 "peak_source": peak_src, "launch_ms": per_launch_ms,
                 "algorithmic_bytes_per_launch": alg}
 
@@ -338,8 +379,8 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=10)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
