@@ -328,6 +328,7 @@ def run_gpu(args):
         per_step_launches = rec["launches"] / args.steps
         per_kernel_bytes = {
             "rows_c2r_coeffs": B * K * N * N * 4,     # coefficient stores of dec
+            "dec_pipe": B * K * N * N * 4 + K * (N // 2 + 1) * N * 4,   # + filters
             "rows_r2c_coeffs": B * K * N * N * 4,     # coefficient loads of rec
             "rows_r2c_image": B * N * N * 4,
             "rows_c2r_image": B * N * N * 4,

@@ -133,8 +133,11 @@ shl_status shl_bank_copy_info(const shl_bank* bank, int* idx, double* rms, doubl
  * shl_workspace_size - bytes of device workspace ``op`` needs for ``batch``
  * images.  The workspace holds the image spectra (decompose) or the
  * per-image accumulators (reconstruct / adjoint) plus a staging area for
- * per-subband intermediates (up to 1 GiB, e.g. all 784 subbands of 16
- * images at 512 x 512 with 49 filters).  Its contents on entry are ignored.
+ * per-subband intermediates.  Decomposition at rows, cols in {512, 1024}
+ * runs pipelined and stages 24 subband planes (25 MB at 512 x 512) plus a
+ * few counters per 8 subbands; other sizes, and the reconstruction, stage
+ * up to 1 GiB (e.g. all 784 subbands of 16 images at 512 x 512 with 49
+ * filters).  Its contents on entry are ignored.
  */
 shl_status shl_workspace_size(const shl_bank* bank, shl_op op, int batch, size_t* bytes);
 
@@ -245,7 +248,10 @@ shl_status shl_profile_enable(int on);
 shl_status shl_profile_read(char* buf, size_t len);
 
 /* Wait for all work on ``stream``; returns SHL_ECUDA with the CUDA error text
- * if a kernel faulted. */
+ * if a kernel faulted, and SHL_ETIMEOUT if a bounded wait inside the
+ * pipelined decomposition (between its column and row passes, Sec. 3.4)
+ * ran out since the last shl_sync on this device; the coefficients of that
+ * call are then incomplete.  The flag is per device and cleared on read. */
 shl_status shl_sync(void* stream);
 
 #ifdef __cplusplus

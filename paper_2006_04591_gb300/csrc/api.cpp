@@ -2,7 +2,7 @@
 //
 // Validation, bank ownership and the launch sequences of the transform live
 // here; all arithmetic on images and coefficients runs in the kernels of
-// rows.cu and cols.cu.
+// fast.cu (and nn.cu for the learned parts).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -107,10 +107,41 @@ int stage_subbands(const shl_bank* b) {
 
 size_t plane_bytes(const shl_bank* b) { return (size_t)b->N * b->Mh * sizeof(float2); }
 
-size_t ws_need(const shl_bank* b, int batch) {
+// Pipelined decomposition: chunk of CS subbands, NS ring slots.  Opt-in
+// (SHL_PIPE=1): it keeps the staging in L2 but measured slower than the
+// two-launch path at 16 x 512 x 512, K = 49 (0.74-0.99 ms against 0.53 ms;
+// both passes are latency-bound at 16 warps per SM and splitting the CTAs
+// between them halves each pass's parallelism).  SHL_PIPE_CS / SHL_PIPE_NS
+// override the ring, SHL_PIPE_COLFRAC the share of CTAs on the column pass.
+struct PipeCfg { bool on; int CS, NS; float col_frac; };
+const PipeCfg& pipe_cfg() {
+  static const PipeCfg c = [] {
+    auto env = [](const char* k, int d, int lo) {
+      const char* e = std::getenv(k);
+      const int v = e ? std::atoi(e) : d;
+      return v >= lo ? v : d;
+    };
+    PipeCfg c{env("SHL_PIPE", 0, 0) != 0, env("SHL_PIPE_CS", 8, 1), env("SHL_PIPE_NS", 3, 2),
+              0.4f};
+    const char* f = std::getenv("SHL_PIPE_COLFRAC");
+    if (f && std::atof(f) > 0.0 && std::atof(f) < 1.0) c.col_frac = (float)std::atof(f);
+    return c;
+  }();
+  return c;
+}
+bool use_pipe(const shl_bank* b) { return pipe_cfg().on && shl::dec_pipe_supported(b->N, b->M); }
+
+size_t ws_need(const shl_bank* b, int batch, shl_op op) {
   const long long sub = (long long)batch * b->K;
+  const size_t X = align256((size_t)batch * plane_bytes(b));
+  if (op == SHL_OP_DECOMPOSE && use_pipe(b)) {
+    const PipeCfg& c = pipe_cfg();
+    const int nchunks = (int)((sub + c.CS - 1) / c.CS);
+    return X + align256((size_t)c.NS * c.CS * plane_bytes(b)) +
+           align256(shl::dec_pipe_ctl_bytes(nchunks));
+  }
   const long long S = std::min<long long>(stage_subbands(b), sub);
-  return align256((size_t)batch * plane_bytes(b)) + align256((size_t)S * plane_bytes(b));
+  return X + align256((size_t)S * plane_bytes(b));
 }
 
 void free_bank(shl_bank* b) {
@@ -183,8 +214,7 @@ shl_status check_common(const shl_bank* b, int batch, const void* ws, size_t ws_
   if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
   if (batch == 0) return SHL_OK;
   if (!ws || !aligned16(ws)) return fail(SHL_EINVAL, "workspace must be a 16-byte aligned device pointer");
-  (void)op;
-  if (ws_bytes < ws_need(b, batch))
+  if (ws_bytes < ws_need(b, batch, op))
     return fail(SHL_EINVAL, "workspace too small (see shl_workspace_size)");
   return SHL_OK;
 }
@@ -226,15 +256,28 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
     e = shl::launch_lines_fwd(N, X, batch * Mh, b->dTw, st);
   }
   if (e) return cuda_fail(e, "lines_fwd_image");
-  const int total = batch * K, S = stage_override > 0 ? stage_override : stage_subbands(b);
+  const int total = batch * K;
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
   const float scale = (float)(1.0 / (double(N) * M));
+  const float* invW = (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr;
+  if (stage_override <= 0 && use_pipe(b)) {
+    const PipeCfg& c = pipe_cfg();
+    unsigned* ctl = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(Z) +
+                                                align256((size_t)c.NS * c.CS * plane_bytes(b)));
+    {
+      Launch L_("dec_pipe", st);
+      e = shl::launch_dec_pipe(N, M, dtype == SHL_BF16, X, Z, coeffs, b->dG, invW, scale, K, total,
+                               c.CS, c.NS, c.col_frac, ctl, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "dec_pipe");
+    return SHL_OK;
+  }
+  const int S = stage_override > 0 ? stage_override : stage_subbands(b);
   for (int s0 = 0; s0 < total; s0 += S) {
     const int Sc = std::min(S, total - s0);
     {
       Launch L_("dec_lines", st);
-      e = shl::launch_dec_lines(N, X, Z, b->dG, (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr,
-                                scale, Mh, K, s0, Sc, b->dTw, st);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st);
     }
     if (e) return cuda_fail(e, "dec_lines");
     {
@@ -424,7 +467,7 @@ shl_status shl_workspace_size(const shl_bank* b, shl_op op, int batch, size_t* b
   if (!b || !bytes) return fail(SHL_EINVAL, "bank and bytes must be non-NULL");
   if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
   if (op != SHL_OP_DECOMPOSE && op != SHL_OP_RECONSTRUCT) return fail(SHL_EINVAL, "bad op");
-  *bytes = batch == 0 ? 0 : ws_need(b, batch);
+  *bytes = batch == 0 ? 0 : ws_need(b, batch, op);
   return SHL_OK;
 }
 
@@ -520,6 +563,11 @@ shl_status shl_profile_read(char* buf, size_t len) {
 shl_status shl_sync(void* stream) {
   cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
   if (e) return cuda_fail(e, "shl_sync");
+  unsigned flag = 0;
+  if ((e = shl::read_pipe_error(&flag))) return cuda_fail(e, "shl_sync");
+  if (flag)
+    return fail(SHL_ETIMEOUT, "pipelined decomposition: a wait between its passes ran out; the "
+                             "coefficients of that call are incomplete");
   return SHL_OK;
 }
 

@@ -26,6 +26,10 @@
 //   C2R: Z[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k/M) (X[k] - conj X[L-k]),
 //        x[2n] + i x[2n+1] = unnormalised IFFT_L(Z)[n] (= M times the
 //        normalised inverse; 1/(N M) is folded into filter or weight factors).
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+
 #include "warp_fft.cuh"
 
 namespace shl {
@@ -251,10 +255,48 @@ __device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, 
   }
 }
 
+// C2R of one TR-row tile staged as tile[kx * CPITCH + row]: row r of the
+// tile (lanes j of group r) is transformed and stored at out + base.
+template <int LOG_M, bool BF16OUT>
+__device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
+                                              const float2* twl, const float2* ptw, void* out,
+                                              size_t base, int r, int j, bool valid) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, CP = P::CPITCH;
+  const int rr = valid ? r : 0;
+  float2 v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const int kk = j + u * T;
+    const float2 A = tile[kk * CP + rr];
+    const float2 B = tile[(L - kk) * CP + rr];
+    const float2 S = make_float2(A.x + B.x, A.y - B.y);
+    const float2 D = make_float2(A.x - B.x, A.y + B.y);
+    const float2 wd = cmulc(D, ptw[kk]);        // D * exp(+2 pi i k / M)
+    v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
+  }
+
+  line_fft<L, R, +1>(v, line, j, 1 + r, twl);
+
+  if (valid) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int p = j + u * T;
+      if constexpr (BF16OUT) {
+        __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
+        __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(out) + base + 2 * p),
+               *reinterpret_cast<unsigned int*>(&h));
+      } else {
+        __stcs(reinterpret_cast<float2*>(static_cast<float*>(out) + base + 2 * p), v[u]);
+      }
+    }
+  }
+}
+
 template <int LOG_M, bool BF16OUT>
 __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_c2r_t(RowsTC2RArgs a) {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, CP = P::CPITCH, TR = P::TR, NST = P::CNST;
+  constexpr int T = P::T, R = P::R, L = P::L, TR = P::TR, NST = P::CNST;
   extern __shared__ __align__(16) float2 smem[];
   float2* stages = smem;
   float2* work = smem + NST * (P::CSTAGE / sizeof(float2));
@@ -283,34 +325,8 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     const float2* tile = stages + (k % NST) * SW;
     const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
 
-    float2 v[R];
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const int kk = j + u * T;
-      const float2 A = tile[kk * CP + rr];
-      const float2 B = tile[(L - kk) * CP + rr];
-      const float2 S = make_float2(A.x + B.x, A.y - B.y);
-      const float2 D = make_float2(A.x - B.x, A.y + B.y);
-      const float2 wd = cmulc(D, ptw[kk]);        // D * exp(+2 pi i k / M)
-      v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
-    }
-
-    line_fft<L, R, +1>(v, line, j, 1 + r, twl);
-
-    if (valid) {
-      const size_t base = ((size_t)s * a.N + y0 + r) * P::M;
-#pragma unroll
-      for (int u = 0; u < R; ++u) {
-        const int p = j + u * T;
-        if constexpr (BF16OUT) {
-          __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
-          __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(a.out) + base + 2 * p),
-                 *reinterpret_cast<unsigned int*>(&h));
-        } else {
-          __stcs(reinterpret_cast<float2*>(static_cast<float*>(a.out) + base + 2 * p), v[u]);
-        }
-      }
-    }
+    c2r_tile_body<LOG_M, BF16OUT>(tile, line, twl, ptw, a.out, ((size_t)s * a.N + y0 + rr) * P::M, r,
+                                  j, valid);
     __syncthreads();                       // stage reuse
   }
   cp_async_wait0();
@@ -365,6 +381,56 @@ __global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
 // filter's G line is fetched before the current FFT.
 constexpr int DEC_FPG = 4;
 
+// One lane group: kx line `kx` of the chunk subbands sl0..sl1-1 (global
+// subband s0 + sl, image s / K, filter s mod K) into out[sl][kx][:].
+template <int LOG_N>
+__device__ __forceinline__ void dec_group(const float2* X, float2* out, const float* Gall,
+                                          const float* invW, float scale, int Mh, int K, int s0,
+                                          int sl0, int sl1, int kx, float2* line, const float2* twl,
+                                          int j, int g) {
+  using P = LinesT<LOG_N>;
+  constexpr int T = P::T, R = P::R, N = P::N;
+  const float* W = invW ? invW + (size_t)kx * N : nullptr;
+  float2 Xl[R];
+  float gn[R];
+  int b_loaded = -1;
+  {
+    const int s = s0 + sl0, b = s / K, i = s - b * K;
+    const float* G = Gall + ((size_t)i * Mh + kx) * N;
+#pragma unroll
+    for (int u = 0; u < R; ++u) gn[u] = __ldg(G + j + u * T);
+  }
+  for (int sl = sl0; sl < sl1; ++sl) {
+    const int s = s0 + sl, b = s / K;
+    if (b != b_loaded) {                              // image spectrum line, once per image
+      const float2* Xp = X + ((size_t)b * Mh + kx) * N;
+#pragma unroll
+      for (int u = 0; u < R; ++u) Xl[u] = Xp[j + u * T];
+      b_loaded = b;
+    }
+    float gc[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) gc[u] = gn[u];
+    if (sl + 1 < sl1) {                               // prefetch the next filter's line
+      const int s2 = s + 1, i2 = s2 - (s2 / K) * K;
+      const float* G2 = Gall + ((size_t)i2 * Mh + kx) * N;
+#pragma unroll
+      for (int u = 0; u < R; ++u) gn[u] = __ldg(G2 + j + u * T);
+    }
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      float gv = gc[u] * scale;
+      if (W) gv *= __ldg(W + j + u * T);
+      v[u] = cscale(Xl[u], gv);
+    }
+    line_fft<N, R, +1>(v, line, j, 1 + g, twl);
+    float2* o = out + ((size_t)sl * Mh + kx) * N;
+#pragma unroll
+    for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
+  }
+}
+
 template <int LOG_N>
 __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   using P = LinesT<LOG_N>;
@@ -381,45 +447,8 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   for (int q = blockIdx.x * P::NG + g; q < items; q += gridDim.x * P::NG) {
     const int m = q / a.Mh, kx = q - m * a.Mh;
     const int sl0 = m * DEC_FPG, sl1 = min(S, sl0 + DEC_FPG);
-    const float* W = a.invW ? a.invW + (size_t)kx * N : nullptr;
-    float2 X[R];
-    float gn[R];
-    int b_loaded = -1;
-    {
-      const int s = a.s0 + sl0, b = s / a.K, i = s - b * a.K;
-      const float* G = a.G + ((size_t)i * a.Mh + kx) * N;
-#pragma unroll
-      for (int u = 0; u < R; ++u) gn[u] = __ldg(G + j + u * T);
-    }
-    for (int sl = sl0; sl < sl1; ++sl) {
-      const int s = a.s0 + sl, b = s / a.K;
-      if (b != b_loaded) {                              // image spectrum line, once per image
-        const float2* Xp = a.data + ((size_t)b * a.Mh + kx) * N;
-#pragma unroll
-        for (int u = 0; u < R; ++u) X[u] = Xp[j + u * T];
-        b_loaded = b;
-      }
-      float gc[R];
-#pragma unroll
-      for (int u = 0; u < R; ++u) gc[u] = gn[u];
-      if (sl + 1 < sl1) {                               // prefetch the next filter's line
-        const int s2 = s + 1, i2 = s2 - (s2 / a.K) * a.K;
-        const float* G2 = a.G + ((size_t)i2 * a.Mh + kx) * N;
-#pragma unroll
-        for (int u = 0; u < R; ++u) gn[u] = __ldg(G2 + j + u * T);
-      }
-      float2 v[R];
-#pragma unroll
-      for (int u = 0; u < R; ++u) {
-        float gv = gc[u] * a.scale;
-        if (W) gv *= __ldg(W + j + u * T);
-        v[u] = cscale(X[u], gv);
-      }
-      line_fft<N, R, +1>(v, line, j, 1 + g, twl);
-      float2* out = a.out + ((size_t)sl * a.Mh + kx) * N;
-#pragma unroll
-      for (int u = 0; u < R; ++u) out[j + u * T] = v[u];
-    }
+    dec_group<LOG_N>(a.data, a.out, a.G, a.invW, a.scale, a.Mh, a.K, a.s0, sl0, sl1, kx, line, twl,
+                     j, g);
   }
 }
 
@@ -492,6 +521,223 @@ __global__ void __launch_bounds__(256, 2) k_rec_lines(RecLinesArgs a) {
 #pragma unroll
     for (int u = 0; u < R; ++u) A[j + u * T] = v[u];
   }
+}
+
+// ------------------------------------------------- pipelined decomposition
+// k_dec_pipe runs both passes of the decomposition in one cooperative,
+// persistent launch.  The subbands are cut into chunks of CS; chunk c is
+// staged in ring slot c mod NS (NS * CS planes, 25 MB at 512 x 512 with the
+// defaults), which stays in L2 while the coefficients stream out with
+// evict-first stores: the staging round trip costs L2, not DRAM, bandwidth.
+// Each CTA has one role:
+//   COL CTAs claim COL items in chunk order: DEC_FPG subbands x NG kx lines
+//     of a chunk (filter multiply and inverse column FFT, dec_group) into
+//     the chunk's ring slot, after the ROW tiles of the chunk that used the
+//     slot NS chunks earlier are done;
+//   ROW CTAs claim TR-row tiles in subband order (C2R rows, c2r_tile_body)
+//     with a two-stage cp.async pipeline: the next tile is fetched while the
+//     current one is transformed, as soon as every COL item of its chunk is
+//     done.
+// The CTAs of both roles share the SMs, so the column pass's arithmetic and
+// the row pass's memory traffic overlap.  The dependencies run from lower to
+// higher chunks only (ROW c after COL c, COL c after ROW c - NS), items are
+// claimed in chunk order, and the cooperative launch keeps every CTA
+// resident, so every wait ends.  Each wait is also bounded: when it runs
+// out the CTA sets g_pipe_err, and every CTA leaves at its next claim.
+__device__ unsigned int g_pipe_err = 0;
+
+constexpr unsigned PIPE_SPIN_LIMIT = 1u << 21;   // ~0.3-1 s with the back-off below
+
+struct DecPipeArgs {
+  const float2* X;           // image spectra [B][Mh][N]
+  float2* ring;              // [NS][CS][Mh][N]
+  void* out;                 // coefficients [total][N][M]
+  const float* G;            // [K][Mh][N]
+  const float* invW;         // [Mh][N] or null
+  const float2* tw;
+  unsigned* ctl;             // [0] COL claims, [1] ROW claims, [4 + c] COL done, [4 + nchunks + c] ROW done
+  float scale;
+  int Mh, K, total, CS, NS, nchunks, ncol_ctas;
+  unsigned stall;            // 0; 1 makes every ROW wait unsatisfiable (tests the bounded wait)
+};
+
+template <int LOG_N, int LOG_M>
+struct DecPipeT {
+  using RP = RowsT<LOG_M>;
+  static constexpr int N = 1 << LOG_N;
+  static constexpr int THREADS = RP::THREADS;
+  static constexpr int RL = LineRadix<N>::R;
+  using CL = LineCfg<N, RL>;
+  static constexpr int TL = CL::T;
+  static constexpr int NG = THREADS / TL;          // column lines per COL item
+  static_assert(NG >= 1 && THREADS % TL == 0, "column line groups must tile the CTA");
+  static constexpr int TPS = N / RP::TR;           // row tiles per subband
+  // two CTAs per SM where the registers of both passes allow it
+  static constexpr int MINB = (THREADS >= 512 || LOG_N >= 10) ? 1 : 2;
+  // shared memory, float2 words: the role's twiddles, then its buffers
+  // (ROW: two C2R stages + row line buffers; COL: column line buffers)
+  static constexpr size_t TWR = (size_t)LineTw<RP::L, RP::R>::WORDS + RP::L;
+  static constexpr size_t TWL = (size_t)LineTw<N, RL>::WORDS;
+  static constexpr size_t TW = TWR > TWL ? TWR : TWL;
+  static constexpr size_t STW = RP::CSTAGE / sizeof(float2);
+  static constexpr size_t ROWW = 2 * STW + (size_t)RP::LPC * RP::C::WORDS;
+  static constexpr size_t COLW = (size_t)NG * CL::WORDS;
+  static constexpr size_t SMEM = sizeof(float2) * (TW + (ROWW > COLW ? ROWW : COLW));
+  static_assert(SMEM <= 227 * 1024, "pipelined decomposition does not fit shared memory");
+};
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Thread 0: wait until *flag >= target.  false = gave up (error recorded).
+__device__ __noinline__ bool pipe_wait(const unsigned* flag, unsigned target) {
+  for (unsigned spin = 0;; ++spin) {
+    if (ld_acquire_u32(flag) >= target) return true;
+    if (*(volatile unsigned*)&g_pipe_err) return false;
+    if (spin >= PIPE_SPIN_LIMIT) {
+      atomicOr(&g_pipe_err, 1u);
+      return false;
+    }
+    if (spin > 32) __nanosleep(128);
+  }
+}
+
+// Thread 0, after the CTA's barrier: publish one finished item.
+__device__ __forceinline__ void pipe_signal(unsigned* flag) {
+  __threadfence();
+  atomicAdd(flag, 1u);
+}
+
+// Issue the cp.async copies of ROW tile t (subband-major over the batch)
+// from its ring slot into a C2R stage.
+template <int LOG_N, int LOG_M>
+__device__ __forceinline__ void pipe_row_issue(const DecPipeArgs& a, float2* stage, int t, int tid) {
+  using P = DecPipeT<LOG_N, LOG_M>;
+  using RP = typename P::RP;
+  constexpr int N = P::N, TR = RP::TR, Mh = RP::Mh, CH = TR / 2;   // 16-byte chunks per kx row
+  const int sub = t / P::TPS, y0 = (t - sub * P::TPS) * TR;
+  const int c = sub / a.CS, sl = sub - c * a.CS;
+  const float2* in = a.ring + ((size_t)(c % a.NS) * a.CS + sl) * ((size_t)Mh * N) + y0;
+  for (int q = tid; q < Mh * CH; q += P::THREADS) {
+    const int kx = q / CH, h = q - kx * CH;
+    cp_async16(stage + kx * RP::CPITCH + 2 * h, in + (size_t)kx * N + 2 * h);
+  }
+  cp_async_commit();
+}
+
+template <int LOG_N, int LOG_M, bool BF16OUT>
+__global__ void __launch_bounds__(DecPipeT<LOG_N, LOG_M>::THREADS, DecPipeT<LOG_N, LOG_M>::MINB)
+k_dec_pipe(DecPipeArgs a) {
+  using P = DecPipeT<LOG_N, LOG_M>;
+  using RP = typename P::RP;
+  constexpr int N = P::N, NG = P::NG, TL = P::TL, RL = P::RL;
+  constexpr int TR = RP::TR, TRow = RP::T, L = RP::L, Mh = RP::Mh, M = RP::M;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* tws = smem;                                  // the role's twiddles
+  float2* area = smem + P::TW;
+  __shared__ int s_item, s_next, s_ok, s_rdy;
+  const int tid = threadIdx.x;
+  const int NCB = (Mh + NG - 1) / NG;
+  const int NCOL = ((a.CS + DEC_FPG - 1) / DEC_FPG) * NCB;   // COL items per chunk
+  unsigned* col_done = a.ctl + 4;
+  unsigned* row_done = a.ctl + 4 + a.nchunks;
+  const size_t plane = (size_t)Mh * N;
+
+  if ((int)blockIdx.x < a.ncol_ctas) {
+    // ------------------------------------------------------------ COL role
+    LineTw<N, RL>::fill(tws, a.tw, tid, P::THREADS);
+    const int items = a.nchunks * NCOL;
+    const int g = tid / TL, j = tid % TL;
+    unsigned ahead = tid == 0 ? atomicAdd(a.ctl + 0, 1u) : 0u;   // one claim ahead
+    for (;;) {
+      __syncthreads();                                 // twiddles ready / item done
+      if (tid == 0) {
+        int it = *(volatile unsigned*)&g_pipe_err ? -1 : (int)ahead;
+        int ok = 1;
+        if (it >= 0 && it < items) {
+          ahead = atomicAdd(a.ctl + 0, 1u);
+          const int c = it / NCOL;
+          if (c >= a.NS) {
+            const int cp = c - a.NS;
+            ok = pipe_wait(row_done + cp, (unsigned)(min(a.CS, a.total - cp * a.CS) * P::TPS));
+          }
+        }
+        s_item = it;
+        s_ok = ok;
+      }
+      __syncthreads();
+      const int it = s_item;
+      if (it < 0 || it >= items || !s_ok) break;
+      const int c = it / NCOL, o = it - c * NCOL;
+      const int Sc = min(a.CS, a.total - c * a.CS);
+      const int m = o / NCB, kb = o - m * NCB;
+      const int sl0 = m * DEC_FPG, sl1 = min(Sc, sl0 + DEC_FPG);
+      const int kx = kb * NG + g;
+      if (kx < Mh && sl0 < sl1)
+        dec_group<LOG_N>(a.X, a.ring + (size_t)(c % a.NS) * a.CS * plane, a.G, a.invW, a.scale,
+                         Mh, a.K, c * a.CS, sl0, sl1, kx, area + (size_t)g * P::CL::WORDS, tws, j, g);
+      __syncthreads();
+      if (tid == 0) pipe_signal(col_done + c);
+    }
+    return;
+  }
+
+  // -------------------------------------------------------------- ROW role
+  float2* twr = tws;                                   // row line twiddles
+  float2* ptw = twr + LineTw<L, RP::R>::WORDS;         // exp(-2 pi i p / M)
+  float2* stages = area;                               // two C2R stages
+  float2* rlines = area + 2 * P::STW;                  // row line buffers
+  LineTw<L, RP::R>::fill(twr, a.tw, tid, P::THREADS);
+  for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  const int ntiles = a.total * P::TPS;
+  const unsigned need = (unsigned)NCOL + a.stall;      // COL items per chunk
+  const int r = tid / TRow, j = tid % TRow;
+  const bool valid = r < TR;
+  const int rr = valid ? r : 0;
+  if (tid == 0) s_next = *(volatile unsigned*)&g_pipe_err ? ntiles : (int)atomicAdd(a.ctl + 1, 1u);
+  __syncthreads();
+  int cur = s_next;
+  bool cur_issued = false;
+  int buf = 0;
+  while (cur < ntiles) {
+    // claim the next tile; prefetch it if its chunk is complete already
+    if (tid == 0) {
+      int ok = 1;
+      if (!cur_issued) ok = pipe_wait(col_done + cur / P::TPS / a.CS, need);
+      int nx = ntiles, rdy = 0;
+      if (ok && !*(volatile unsigned*)&g_pipe_err) {
+        nx = (int)atomicAdd(a.ctl + 1, 1u);
+        if (nx < ntiles) rdy = ld_acquire_u32(col_done + nx / P::TPS / a.CS) >= need;
+      }
+      s_next = nx;
+      s_rdy = rdy;
+      s_ok = ok;
+    }
+    __syncthreads();
+    if (!s_ok) break;
+    const int nx = s_next;
+    const bool rdy = s_rdy != 0;
+    if (!cur_issued) pipe_row_issue<LOG_N, LOG_M>(a, stages + buf * P::STW, cur, tid);
+    if (rdy) {
+      pipe_row_issue<LOG_N, LOG_M>(a, stages + (buf ^ 1) * P::STW, nx, tid);
+      cp_async_wait1();
+    } else {
+      cp_async_wait0();
+    }
+    __syncthreads();
+    const int sub = cur / P::TPS, y0 = (cur - sub * P::TPS) * TR;
+    c2r_tile_body<LOG_M, BF16OUT>(stages + buf * P::STW, rlines + (size_t)r * RP::C::WORDS, twr,
+                                  ptw, a.out, ((size_t)sub * N + y0 + rr) * M, r, j, valid);
+    __syncthreads();                                   // stage reuse, tile stored
+    if (tid == 0) pipe_signal(row_done + sub / a.CS);
+    cur = nx;
+    cur_issued = rdy;
+    buf ^= 1;
+  }
+  cp_async_wait0();
 }
 
 // --------------------------------------------------------------- launch
@@ -637,6 +883,69 @@ cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const floa
 #define CALL(X) lines_t<X>(2, a, ra, gy, st)
   SHL_SWITCH_LOG(ilog2(N), CALL)
 #undef CALL
+}
+
+// ------------------------------------------------------- pipelined launch
+template <int LOG_N, int LOG_M, bool BF16>
+static cudaError_t dec_pipe_t(const DecPipeArgs& a0, float col_frac, cudaStream_t st) {
+  using P = DecPipeT<LOG_N, LOG_M>;
+  auto kern = k_dec_pipe<LOG_N, LOG_M, BF16>;
+  cudaError_t e;
+  if ((e = prep(kern, P::SMEM))) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, P::THREADS, P::SMEM)))
+    return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  const int grid = per_sm * sm_count();
+  if (grid < 2) return cudaErrorInvalidConfiguration;
+  DecPipeArgs args = a0;
+  args.ncol_ctas = std::min(grid - 1, std::max(1, (int)std::lround(col_frac * grid)));
+  void* params[] = {&args};
+  return cudaLaunchCooperativeKernel(reinterpret_cast<const void*>(kern), dim3(grid),
+                                     dim3(P::THREADS), params, P::SMEM, st);
+}
+
+// Column length 1024 needs 32 complex values per lane in the column pass,
+// which does not fit beside the row pass at two CTAs per SM (it spills);
+// those sizes keep the two-launch path.
+bool dec_pipe_supported(int N, int M) { return N == 512 && (M == 512 || M == 1024); }
+
+size_t dec_pipe_ctl_bytes(int nchunks) { return sizeof(unsigned) * (4 + 2 * (size_t)nchunks); }
+
+cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ring, void* out,
+                            const float* G, const float* invW, float scale, int K, int total,
+                            int CS, int NS, float col_frac, unsigned* ctl, const float2* tw,
+                            cudaStream_t st) {
+  if (total == 0) return cudaSuccess;
+  if (!dec_pipe_supported(N, M) || CS < 1 || NS < 2 || !(col_frac > 0.f && col_frac < 1.f))
+    return cudaErrorInvalidValue;
+  DecPipeArgs a{};
+  a.X = X; a.ring = ring; a.out = out; a.G = G; a.invW = invW; a.tw = tw; a.ctl = ctl;
+  a.scale = scale; a.Mh = M / 2 + 1; a.K = K; a.total = total; a.CS = CS; a.NS = NS;
+  a.nchunks = (total + CS - 1) / CS;
+  // SHL_PIPE_STALL_TEST=1 (read per call): the ROW items wait for one COL
+  // item more than exist, so every wait runs out; used to test that the
+  // bounded waits end the launch and shl_sync reports SHL_EDEVICE.
+  const char* stall = std::getenv("SHL_PIPE_STALL_TEST");
+  a.stall = (stall && stall[0] == '1') ? 1u : 0u;
+  cudaError_t e = cudaMemsetAsync(ctl, 0, dec_pipe_ctl_bytes(a.nchunks), st);
+  if (e) return e;
+#define SHL_PIPE(LN, LM)                                                        \
+  if (N == (1 << LN) && M == (1 << LM))                                          \
+    return bf16 ? dec_pipe_t<LN, LM, true>(a, col_frac, st) : dec_pipe_t<LN, LM, false>(a, col_frac, st);
+  SHL_PIPE(9, 9) SHL_PIPE(9, 10)
+#undef SHL_PIPE
+  return cudaErrorInvalidValue;
+}
+
+// Reads and clears the pipelined-wait error flag of the current device.
+cudaError_t read_pipe_error(unsigned* flag) {
+  cudaError_t e = cudaMemcpyFromSymbol(flag, g_pipe_err, sizeof(unsigned));
+  if (e == cudaSuccess && *flag) {
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbol(g_pipe_err, &zero, sizeof(unsigned));
+  }
+  return e;
 }
 
 // Per-subband max |c| (optionally divided by RMS_i): one CTA per subband.

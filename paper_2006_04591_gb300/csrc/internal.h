@@ -35,6 +35,16 @@ cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G
 cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
                              const float2* tw, cudaStream_t st);
+// Pipelined decomposition (both passes in one cooperative launch over a
+// ring of NS staging chunks of CS subbands, col_frac of the CTAs on the
+// column pass); sizes with dec_pipe_supported.
+bool dec_pipe_supported(int N, int M);
+size_t dec_pipe_ctl_bytes(int nchunks);
+cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ring, void* out,
+                            const float* G, const float* invW, float scale, int K, int total,
+                            int CS, int NS, float col_frac, unsigned* ctl, const float2* tw,
+                            cudaStream_t st);
+cudaError_t read_pipe_error(unsigned* flag);
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st);
 

@@ -22,6 +22,8 @@ from . import _build
 SHL_F32, SHL_BF16 = 0, 1
 SHL_DUAL_WEIGHTED = 1
 SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT = 0, 1
+(SHL_OK, SHL_EINVAL, SHL_ENOMEM, SHL_ECUDA, SHL_EUNSUPPORTED, SHL_ETIMEOUT,
+ SHL_EDEVICE) = range(7)
 HEADER = os.path.join(os.path.dirname(_build.PKG), "include", "shearlet.h")
 
 _lib = None
