@@ -70,6 +70,7 @@ typedef enum { SHL_F32 = 0, SHL_BF16 = 1 } shl_dtype;
 typedef enum {
   SHL_OP_DECOMPOSE = 0,
   SHL_OP_RECONSTRUCT = 1, /* also shl_adjoint */
+  SHL_OP_SHRINK = 2,      /* shl_shrink */
 } shl_op;
 
 typedef struct shl_bank shl_bank;
@@ -204,7 +205,7 @@ shl_status shl_decompose_masked(const shl_bank* bank, const float* f_masked,
  * shl_reconstruct - shearlet reconstruction (Sec. 3.4, Alg. "Shearlet
  * reconstruction" and the ``tfshearrec2D`` listing; Eq. 2.7):
  *   x[b] = IFFT2( (1/W) * sum_{i=0..K-1} G_i * FFT2(T(c[b][i])) )
- * summed in the fixed order i = 0..K-1 in float32.  T is the hard
+ * summed in float32 in a fixed order (the same bits on every run).  T is the hard
  * threshold of Sec. 4.2 applied while the coefficients are read: an entry
  * with |c| < thresh[b][i] becomes 0 (ties are kept).
  *   coeffs  device [batch][K][rows][cols] of dtype.
@@ -224,6 +225,27 @@ shl_status shl_reconstruct(const shl_bank* bank, const void* coeffs, shl_dtype d
 shl_status shl_adjoint(const shl_bank* bank, const void* coeffs, shl_dtype dtype, int batch,
                        const float* thresh, float* x_out, void* ws, size_t ws_bytes,
                        void* stream);
+
+/*
+ * shl_shrink - one hard-threshold step of denoising (Sec. 4.2) or of the
+ * inpainting iteration (Sec. 4.3, Alg. "Shearlet inpainting by iterative
+ * hard thresholding") without storing coefficients:
+ *   x_out[b] = IFFT2( (1/W) sum_i G_i FFT2( T_b,i( IFFT2( G_i FFT2(u[b]) ) ) ) )
+ *   u = x                                 (mask == NULL; f_est ignored)
+ *   u = mask * (x - f_est) + f_est        (mask != NULL: x = f_masked)
+ * T_b,i zeroes coefficients with |c| < thresh[b][i] (ties kept).  The
+ * coefficients live only in registers: each staged half-spectrum row tile
+ * is inverse-transformed, thresholded and transformed back in place, so
+ * the result equals shl_decompose (float32) followed by
+ * shl_reconstruct(thresh) while moving ~2/3 of their DRAM bytes.
+ *   x, f_est  device float32 [batch][rows][cols]; mask device uint8 or NULL.
+ *   thresh    device float32 [batch][K].
+ *   x_out     device float32 [batch][rows][cols]; may alias x or f_est.
+ *   ws        device workspace of >= shl_workspace_size(SHRINK) bytes.
+ */
+shl_status shl_shrink(const shl_bank* bank, const float* x, const unsigned char* mask,
+                      const float* f_est, int batch, const float* thresh, float* x_out, void* ws,
+                      size_t ws_bytes, void* stream);
 
 /*
  * shl_subband_absmax - out[b][i] = max_{y,x} |c[b][i][y][x]| / scale_i with

@@ -2,10 +2,13 @@
 (Sec. 4.3, Alg. "Shearlet inpainting by iterative hard thresholding") on the
 GPU through libshearlet.
 
-Every transform, threshold and residual step runs in the library's kernels:
-the hard threshold is applied while the reconstruction reads the
-coefficients, and the inpainting residual M (f_masked - f) + f is formed while
-the decomposition reads its input.  Thresholds are per (image, subband):
+Every transform, threshold and residual step runs in the library's kernels.
+With float32 coefficients both loops call shl_shrink, which thresholds each
+row tile of coefficients in registers between the decomposition's and the
+reconstruction's row passes, so the coefficients never reach memory; with
+bfloat16 coefficients (or fused=False) the decomposition stores them and the
+reconstruction applies the threshold while reading them.  The inpainting
+residual M (f_masked - f) + f is formed while the first pass reads its input.  Thresholds are per (image, subband):
   denoising   delta_i = factor_{scale(i)} * sigma * RMS_i, low-pass kept;
   inpainting  delta_t * RMS_i for every subband, delta_t = delta_init lambda^t,
               lambda = (delta_min / delta_init)^(1 / (T - 1)),
@@ -17,7 +20,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-from .shearlet import SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT, Bank
+from .shearlet import SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT, SHL_OP_SHRINK, Bank
 
 
 def denoise_thresholds(bank: Bank, sigma: float, factors, batch: int) -> torch.Tensor:
@@ -32,11 +35,14 @@ def denoise_thresholds(bank: Bank, sigma: float, factors, batch: int) -> torch.T
 
 
 def denoise(bank: Bank, x_noisy: torch.Tensor, sigma: float, factors=3.0,
-            coeff_dtype=torch.float32) -> torch.Tensor:
+            coeff_dtype=torch.float32, fused=True, ws=None) -> torch.Tensor:
     """SH^{-1} T_delta SH x for a batch [B, N, M] (float32)."""
     B = x_noisy.shape[0]
+    th = denoise_thresholds(bank, sigma, factors, B)
+    if fused and coeff_dtype == torch.float32:
+        return bank.shrink(x_noisy, th, ws=ws)
     c = bank.decompose(x_noisy, dtype=coeff_dtype)
-    return bank.reconstruct(c, thresh=denoise_thresholds(bank, sigma, factors, B))
+    return bank.reconstruct(c, thresh=th)
 
 
 def iht_start_threshold(bank: Bank, f_masked: torch.Tensor, coeffs=None) -> torch.Tensor:
@@ -47,7 +53,7 @@ def iht_start_threshold(bank: Bank, f_masked: torch.Tensor, coeffs=None) -> torc
 
 def iht_inpaint(bank: Bank, f_masked: torch.Tensor, mask: torch.Tensor, iterations: int,
                 delta_min: float = 0.02, delta_init=None, coeff_dtype=torch.float32,
-                f_init=None):
+                f_init=None, fused=True):
     """Alg. "Shearlet inpainting by iterative hard thresholding" for a batch.
 
     f_masked: [B, N, M] float32; mask: [B, N, M] (nonzero = observed).
@@ -57,11 +63,12 @@ def iht_inpaint(bank: Bank, f_masked: torch.Tensor, mask: torch.Tensor, iteratio
     dev = f_masked.device
     mask_u8 = (mask != 0).to(torch.uint8).contiguous()
     f_masked = f_masked.contiguous().float()
-    coeffs = torch.empty((B, bank.K, bank.rows, bank.cols), dtype=coeff_dtype, device=dev)
-    ws_d = bank.workspace(SHL_OP_DECOMPOSE, B)
-    ws_r = bank.workspace(SHL_OP_RECONSTRUCT, B)
+    fused = fused and coeff_dtype == torch.float32
+    coeffs = None
+    if delta_init is None or not fused:
+        coeffs = torch.empty((B, bank.K, bank.rows, bank.cols), dtype=coeff_dtype, device=dev)
     if delta_init is None:
-        delta_init = iht_start_threshold(bank, f_masked)
+        delta_init = iht_start_threshold(bank, f_masked, coeffs)
     delta_init = torch.as_tensor(delta_init, dtype=torch.float64, device="cpu").reshape(-1)
     if delta_init.numel() == 1:
         delta_init = delta_init.expand(B)
@@ -74,6 +81,14 @@ def iht_inpaint(bank: Bank, f_masked: torch.Tensor, mask: torch.Tensor, iteratio
     th = torch.from_numpy((deltas[:, :, None] * rms[None, None, :]).astype(np.float32)).to(dev)
     f = torch.zeros_like(f_masked) if f_init is None else f_init.contiguous().float().clone()
     g = torch.empty_like(f)
+    if fused:
+        ws = bank.workspace(SHL_OP_SHRINK, B)
+        for t in range(T):
+            bank.shrink(f_masked, th[t], mask_u8=mask_u8, f_est=f, out=g, ws=ws)
+            f, g = g, f
+        return f
+    ws_d = bank.workspace(SHL_OP_DECOMPOSE, B)
+    ws_r = bank.workspace(SHL_OP_RECONSTRUCT, B)
     for t in range(T):
         bank.decompose_masked(f_masked, mask_u8, f, out=coeffs, ws=ws_d)
         bank.reconstruct(coeffs, thresh=th[t], out=g, ws=ws_r)

@@ -141,6 +141,8 @@ size_t ws_need(const shl_bank* b, int batch, shl_op op) {
            align256(shl::dec_pipe_ctl_bytes(nchunks));
   }
   const long long S = std::min<long long>(stage_subbands(b), sub);
+  if (op == SHL_OP_SHRINK)   // image spectra and accumulators both live to the end
+    return 2 * X + align256((size_t)S * plane_bytes(b));
   return X + align256((size_t)S * plane_bytes(b));
 }
 
@@ -291,6 +293,15 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   return SHL_OK;
 }
 
+// Reconstruction-style chunks (whole images when the staging area holds K
+// subbands, else filter ranges inside one image), shared by reconstruct_impl
+// and shrink_impl.
+int next_chunk(int s0, int total, int S, int K) {
+  if (S >= K) return std::min((S / K) * K, total - s0);
+  const int img_end = (s0 / K + 1) * K;
+  return std::min(S, img_end - s0);
+}
+
 // Reconstruction chunks: whole images when the staging area holds K
 // subbands, otherwise filter ranges inside one image (partial sums are
 // carried in the accumulator plane of that image).
@@ -315,13 +326,7 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
   const float scale = (float)(1.0 / (double(N) * M));
   cudaError_t e;
   for (int s0 = 0; s0 < total;) {
-    int Sc;
-    if (S >= K) {
-      Sc = std::min((S / K) * K, total - s0);
-    } else {
-      const int img_end = (s0 / K + 1) * K;
-      Sc = std::min(S, img_end - s0);
-    }
+    const int Sc = next_chunk(s0, total, S, K);
     {
       Launch L_("rows_r2c_coeffs", st);
       e = shl::launch_rows_r2c_t(M, dtype == SHL_BF16 ? shl::IN_BF16 : shl::IN_F32,
@@ -335,6 +340,64 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
       Launch L_("rec_lines", st);
       e = shl::launch_rec_lines(N, Z, A, b->dG, weights ? b->dInvW : nullptr, scale, Mh, K, s0,
                                 Sc, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "rec_lines");
+    s0 += Sc;
+  }
+  {
+    Launch L_("rows_c2r_image", st);
+    e = shl::launch_rows_c2r_t(M, false, A, x_out, N, batch, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "rows_c2r_image");
+  return SHL_OK;
+}
+
+shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* mask,
+                       const float* fest, int batch, const float* thresh, float* x_out, void* ws,
+                       size_t ws_bytes, void* stream) {
+  shl_status s = check_common(b, batch, ws, ws_bytes, SHL_OP_SHRINK);
+  if (s != SHL_OK || batch == 0) return s;
+  if (!x || !x_out || !thresh || !aligned16(x) || !aligned16(x_out))
+    return fail(SHL_EINVAL, "x, thresh and x_out must be device pointers (x, x_out 16-byte aligned)");
+  if (reinterpret_cast<uintptr_t>(thresh) & 3u) return fail(SHL_EINVAL, "thresh must be 4-byte aligned");
+  if (mask && (!fest || !aligned16(fest) || !aligned16(mask)))
+    return fail(SHL_EINVAL, "mask and f_est must be 16-byte aligned device pointers");
+  DevGuard g(b->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
+  const size_t img = align256((size_t)batch * plane_bytes(b));
+  float2* X = static_cast<float2*>(ws);
+  float2* A = reinterpret_cast<float2*>(static_cast<char*>(ws) + img);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) + 2 * img);
+  const float scale = (float)(1.0 / (double(N) * M));
+  cudaError_t e;
+  {
+    Launch L_("rows_r2c_image", st);
+    e = shl::launch_rows_r2c_t(M, mask ? shl::IN_MASKED : shl::IN_F32, false, x, mask, fest,
+                               nullptr, X, N, batch, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "rows_r2c_image");
+  {
+    Launch L_("lines_fwd_image", st);
+    e = shl::launch_lines_fwd(N, X, batch * Mh, b->dTw, st);
+  }
+  if (e) return cuda_fail(e, "lines_fwd_image");
+  const int total = batch * K, S = stage_subbands(b);
+  for (int s0 = 0; s0 < total;) {
+    const int Sc = next_chunk(s0, total, S, K);
+    {
+      Launch L_("dec_lines", st);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, nullptr, scale, Mh, K, s0, Sc, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "dec_lines");
+    {
+      Launch L_("rows_shrink", st);
+      e = shl::launch_rows_shrink_t(M, Z, thresh + s0, N, Sc, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "rows_shrink");
+    {
+      Launch L_("rec_lines", st);
+      e = shl::launch_rec_lines(N, Z, A, b->dG, b->dInvW, scale, Mh, K, s0, Sc, b->dTw, st);
     }
     if (e) return cuda_fail(e, "rec_lines");
     s0 += Sc;
@@ -466,7 +529,8 @@ shl_status shl_bank_copy_info(const shl_bank* b, int* idx, double* rms, double* 
 shl_status shl_workspace_size(const shl_bank* b, shl_op op, int batch, size_t* bytes) {
   if (!b || !bytes) return fail(SHL_EINVAL, "bank and bytes must be non-NULL");
   if (batch < 0) return fail(SHL_EINVAL, "batch must be >= 0");
-  if (op != SHL_OP_DECOMPOSE && op != SHL_OP_RECONSTRUCT) return fail(SHL_EINVAL, "bad op");
+  if (op != SHL_OP_DECOMPOSE && op != SHL_OP_RECONSTRUCT && op != SHL_OP_SHRINK)
+    return fail(SHL_EINVAL, "bad op");
   *bytes = batch == 0 ? 0 : ws_need(b, batch, op);
   return SHL_OK;
 }
@@ -495,6 +559,12 @@ shl_status shl_adjoint(const shl_bank* b, const void* coeffs, shl_dtype dtype, i
                        const float* thresh, float* x_out, void* ws, size_t ws_bytes,
                        void* stream) {
   return reconstruct_impl(b, coeffs, dtype, batch, thresh, x_out, ws, ws_bytes, stream, false);
+}
+
+shl_status shl_shrink(const shl_bank* b, const float* x, const unsigned char* mask,
+                      const float* f_est, int batch, const float* thresh, float* x_out, void* ws,
+                      size_t ws_bytes, void* stream) {
+  return shrink_impl(b, x, mask, f_est, batch, thresh, x_out, ws, ws_bytes, stream);
 }
 
 shl_status shl_subband_absmax(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,

@@ -126,11 +126,54 @@ __device__ __forceinline__ void r2c_issue(const RowsTArgs& a, char* stage, int t
   }
 }
 
+// Forward half of a row tile: v[u] = z[j + u T] (two reals packed per
+// complex) of row r -> R2C (line FFT and conjugate-pair split) -> the
+// transposed tile in shared memory -> out[kx * N + row] for the TR rows.
+// Ends with a CTA barrier, after which the line and tile buffers are free.
+template <int LOG_M>
+__device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], float2* line,
+                                                float2* tile, const float2* twl, const float2* ptw,
+                                                float2* out, int N, int r, int j, bool valid,
+                                                int tid) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, TR = P::TR, TP = P::TP;
+  line_fft<L, R, -1>(v, line, j, 1 + r, twl);
+
+  // conjugate-pair split needs Z[L - k]: publish the natural-order line
+  group_sync<T>(1 + r);
+  line_store<L, R>(v, line, j);
+  group_sync<T>(1 + r);
+  float2 mir[R];
+  line_load_mirror<L, R>(mir, line, j);
+  const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], kept by lane j == 0
+#pragma unroll
+  for (int u = 0; u < R; ++u) {
+    const float2 A = v[u], B = mir[u];
+    const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
+    const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
+    v[u] = cadd(E, cmul(O, ptw[j + u * T]));
+  }
+  __syncthreads();                       // line buffers become the tile
+  if (valid) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) tile[(j + u * T) * TP + r] = v[u];
+    if (j == 0) tile[L * TP + r] = nyq;
+  }
+  __syncthreads();
+  // transposed store: two rows of one kx per 16-byte store
+  for (int idx = tid; idx < Mh * (TR / 2); idx += P::THREADS) {
+    const int kx = idx / (TR / 2), q = 2 * (idx % (TR / 2));
+    const float2 lo = tile[kx * TP + q], hi = tile[kx * TP + q + 1];
+    *reinterpret_cast<float4*>(out + (size_t)kx * N + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
+  }
+  __syncthreads();
+}
+
 template <int LOG_M, int INM, bool THRESH>
 __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_r2c_t(RowsTArgs a) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, M = P::M;
-  constexpr int TR = P::TR, TP = P::TP;
+  constexpr int TR = P::TR;
   constexpr size_t SB = r2c_stage_bytes<LOG_M, INM>();
   constexpr int NST = r2c_nst<LOG_M, INM>();
   extern __shared__ __align__(16) float2 smem[];
@@ -200,37 +243,8 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
       v[u] = valid ? z : make_float2(0.f, 0.f);
     }
 
-    line_fft<L, R, -1>(v, line, j, 1 + r, twl);
-
-    // conjugate-pair split needs Z[L - k]: publish the natural-order line
-    group_sync<T>(1 + r);
-    line_store<L, R>(v, line, j);
-    group_sync<T>(1 + r);
-    float2 mir[R];
-    line_load_mirror<L, R>(mir, line, j);
-    const float2 nyq = make_float2(v[0].x - v[0].y, 0.f);   // X[L], kept by lane j == 0
-#pragma unroll
-    for (int u = 0; u < R; ++u) {
-      const float2 A = v[u], B = mir[u];
-      const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
-      const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-      v[u] = cadd(E, cmul(O, ptw[j + u * T]));
-    }
-    __syncthreads();                       // line buffers become the tile
-    if (valid) {
-#pragma unroll
-      for (int u = 0; u < R; ++u) tile[(j + u * T) * TP + r] = v[u];
-      if (j == 0) tile[L * TP + r] = nyq;
-    }
-    __syncthreads();
-    // transposed store: two rows of one kx per 16-byte store
-    float2* out = a.out + (size_t)s * Mh * a.N + y0;
-    for (int idx = tid; idx < Mh * (TR / 2); idx += P::THREADS) {
-      const int kx = idx / (TR / 2), q = 2 * (idx % (TR / 2));
-      const float2 lo = tile[kx * TP + q], hi = tile[kx * TP + q + 1];
-      *reinterpret_cast<float4*>(out + (size_t)kx * a.N + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
-    }
-    __syncthreads();                       // tile / stage reuse
+    r2c_tile_finish<LOG_M>(v, line, tile, twl, ptw, a.out + (size_t)s * Mh * a.N + y0, a.N, r, j,
+                           valid, tid);    // ends with a barrier: tile and stage reusable
   }
   cp_async_wait0();
 }
@@ -255,16 +269,17 @@ __device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, 
   }
 }
 
-// C2R of one TR-row tile staged as tile[kx * CPITCH + row]: row r of the
-// tile (lanes j of group r) is transformed and stored at out + base.
-template <int LOG_M, bool BF16OUT>
-__device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
-                                              const float2* twl, const float2* ptw, void* out,
-                                              size_t base, int r, int j, bool valid) {
+// C2R of one TR-row tile staged as tile[kx * CPITCH + row]: on return v[u]
+// holds (x[2p], x[2p+1]), p = j + u T, of row r of the tile (lanes j of
+// group r); unnormalised (the 1/(N M) sits in the filter or weight factors).
+template <int LOG_M>
+__device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* line,
+                                                 const float2* twl, const float2* ptw, int r,
+                                                 int j, bool valid,
+                                                 float2 (&v)[RowsT<LOG_M>::R]) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, CP = P::CPITCH;
   const int rr = valid ? r : 0;
-  float2 v[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int kk = j + u * T;
@@ -275,9 +290,18 @@ __device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
     const float2 wd = cmulc(D, ptw[kk]);        // D * exp(+2 pi i k / M)
     v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
   }
-
   line_fft<L, R, +1>(v, line, j, 1 + r, twl);
+}
 
+// C2R of one staged tile and the store of row r to out + base.
+template <int LOG_M, bool BF16OUT>
+__device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
+                                              const float2* twl, const float2* ptw, void* out,
+                                              size_t base, int r, int j, bool valid) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R;
+  float2 v[R];
+  c2r_tile_compute<LOG_M>(tile, line, twl, ptw, r, j, valid, v);
   if (valid) {
 #pragma unroll
     for (int u = 0; u < R; ++u) {
@@ -328,6 +352,65 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     c2r_tile_body<LOG_M, BF16OUT>(tile, line, twl, ptw, a.out, ((size_t)s * a.N + y0 + rr) * P::M, r,
                                   j, valid);
     __syncthreads();                       // stage reuse
+  }
+  cp_async_wait0();
+}
+
+// Row pass of the fused denoise / IHT step, in place on the staged half
+// spectra of the chunk: each TR-row tile is C2R'd to its coefficient rows in
+// registers, hard-thresholded (T_delta of Sec. 4.2: zero |c| < thresh[s],
+// ties kept, the same float32 compare as the threshold-on-read R2C), and
+// R2C'd back to the same place.  The coefficients never reach memory.
+struct RowsShrinkArgs {
+  float2* z;                 // [nsub][Mh][N], read and rewritten
+  const float* thresh;       // [nsub]
+  const float2* tw;
+  int N, nsub;
+};
+
+template <int LOG_M>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB)
+k_rows_shrink_t(RowsShrinkArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, TR = P::TR, NST = P::CNST;
+  extern __shared__ __align__(16) float2 smem[];
+  float2* stages = smem;
+  float2* work = smem + NST * (P::CSTAGE / sizeof(float2));
+  float2* twl = work + P::WORK / sizeof(float2);
+  float2* ptw = twl + LineTw<L, R>::WORDS;
+  const int tid = threadIdx.x;
+  const int r = tid / T, j = tid % T;
+  const bool valid = r < TR;
+  float2* line = work + (size_t)r * P::C::WORDS;
+  const int tiles_per_sub = a.N / TR;
+  const int ntiles = a.nsub * tiles_per_sub;
+  constexpr size_t SW = P::CSTAGE / sizeof(float2);
+  const RowsTC2RArgs ca{a.z, nullptr, a.tw, a.N, a.nsub};
+
+  LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
+  for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M>(ca, stages, blockIdx.x, tid);
+  cp_async_commit();
+  int k = 0;
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    const int tn = NST == 2 ? t + gridDim.x : t;
+    if (tn < ntiles) c2r_issue<LOG_M>(ca, stages + ((k + 1) % NST) * SW, tn, tid);
+    cp_async_commit();
+    if (NST == 2) cp_async_wait1(); else cp_async_wait0();
+    __syncthreads();
+    const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
+    float2 v[R];
+    c2r_tile_compute<LOG_M>(stages + (k % NST) * SW, line, twl, ptw, r, j, valid, v);
+    const float tau = __ldg(a.thresh + s);
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      if (fabsf(v[u].x) < tau) v[u].x = 0.f;
+      if (fabsf(v[u].y) < tau) v[u].y = 0.f;
+    }
+    // the forward line FFT reuses the group's own line buffer after a group
+    // sync; the CTA-wide tile reuse is fenced inside r2c_tile_finish
+    r2c_tile_finish<LOG_M>(v, line, work, twl, ptw, a.z + (size_t)s * Mh * a.N + y0, a.N, r, j,
+                           valid, tid);    // ends with a barrier: tile and stage reusable
   }
   cp_async_wait0();
 }
@@ -796,6 +879,19 @@ static cudaError_t c2r_t(bool bf16, const RowsTC2RArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+template <int LOG_M>
+static cudaError_t shrink_t(const RowsShrinkArgs& a, cudaStream_t st) {
+  using P = RowsT<LOG_M>;
+  const int ntiles = a.nsub * (a.N / P::TR);
+  if (ntiles == 0) return cudaSuccess;
+  const int grid = std::min(ntiles, sm_count() * P::MINB);
+  const size_t sm = P::CNST * P::CSTAGE + P::WORK + P::TWB;
+  cudaError_t e;
+  if ((e = prep(k_rows_shrink_t<LOG_M>, sm))) return e;
+  k_rows_shrink_t<LOG_M><<<grid, P::THREADS, sm, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int LOG_N>
 static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra, int grid_y,
                            cudaStream_t st) {
@@ -847,6 +943,14 @@ cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int
                               const float2* tw, cudaStream_t st) {
   RowsTC2RArgs a{in, out, tw, N, nsub};
 #define CALL(X) c2r_t<X>(bf16, a, st)
+  SHL_SWITCH_LOG(ilog2(M), CALL)
+#undef CALL
+}
+
+cudaError_t launch_rows_shrink_t(int M, float2* z, const float* thresh, int N, int nsub,
+                                 const float2* tw, cudaStream_t st) {
+  RowsShrinkArgs a{z, thresh, tw, N, nsub};
+#define CALL(X) shrink_t<X>(a, st)
   SHL_SWITCH_LOG(ilog2(M), CALL)
 #undef CALL
 }

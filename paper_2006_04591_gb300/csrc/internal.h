@@ -28,6 +28,10 @@ cudaError_t launch_rows_r2c_t(int M, InMode mode, bool thresh, const void* in, c
                               const float2* tw, cudaStream_t st);
 cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int N, int nsub,
                               const float2* tw, cudaStream_t st);
+// In place on [nsub][Mh][N] half spectra: C2R rows -> zero |c| < thresh[s]
+// -> R2C rows (the fused threshold of the denoise / IHT step).
+cudaError_t launch_rows_shrink_t(int M, float2* z, const float* thresh, int N, int nsub,
+                                 const float2* tw, cudaStream_t st);
 cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, cudaStream_t st);
 cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
                              float scale, int Mh, int K, int s0, int S, const float2* tw,

@@ -33,7 +33,7 @@ import torch
 
 from . import apps, nn, synth
 from .autograd import shearlet_dec, shearlet_rec
-from .shearlet import SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT, Bank
+from .shearlet import SHL_OP_SHRINK, Bank
 
 
 def unrolled_iht(bank: Bank, f_masked, mask_u8, deltas, tau, rms):
@@ -47,17 +47,14 @@ def unrolled_iht(bank: Bank, f_masked, mask_u8, deltas, tau, rms):
 
 
 def hard_iht(bank: Bank, f_masked, mask_u8, thresholds, out_each=None):
-    """Hard-threshold iterations with given absolute thresholds [T, B, K]."""
+    """Hard-threshold iterations with given absolute thresholds [T, B, K]
+    (one shl_shrink per iteration: the coefficients stay in registers)."""
     B = f_masked.shape[0]
-    coeffs = torch.empty((B, bank.K, bank.rows, bank.cols), dtype=torch.float32,
-                         device=f_masked.device)
-    ws_d = bank.workspace(SHL_OP_DECOMPOSE, B)
-    ws_r = bank.workspace(SHL_OP_RECONSTRUCT, B)
+    ws = bank.workspace(SHL_OP_SHRINK, B)
     f = torch.zeros_like(f_masked)
     g = torch.empty_like(f)
     for t in range(thresholds.shape[0]):
-        bank.decompose_masked(f_masked, mask_u8, f, out=coeffs, ws=ws_d)
-        bank.reconstruct(coeffs, thresh=thresholds[t], out=g, ws=ws_r)
+        bank.shrink(f_masked, thresholds[t], mask_u8=mask_u8, f_est=f, out=g, ws=ws)
         f, g = g, f
         if out_each is not None:
             out_each(t, f)

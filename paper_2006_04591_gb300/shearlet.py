@@ -21,7 +21,7 @@ from . import _build
 
 SHL_F32, SHL_BF16 = 0, 1
 SHL_DUAL_WEIGHTED = 1
-SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT = 0, 1
+SHL_OP_DECOMPOSE, SHL_OP_RECONSTRUCT, SHL_OP_SHRINK = 0, 1, 2
 (SHL_OK, SHL_EINVAL, SHL_ENOMEM, SHL_ECUDA, SHL_EUNSUPPORTED, SHL_ETIMEOUT,
  SHL_EDEVICE) = range(7)
 HEADER = os.path.join(os.path.dirname(_build.PKG), "include", "shearlet.h")
@@ -65,6 +65,7 @@ def lib():
         "shl_decompose_noalloc": (i, [vp, vp, i, vp, i, i, vp]),
         "shl_reconstruct": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
         "shl_adjoint": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
+        "shl_shrink": (i, [vp, vp, vp, vp, i, vp, vp, vp, sz, vp]),
         "shl_subband_absmax": (i, [vp, vp, i, i, i, vp, vp]),
         "shl_sync": (i, [vp]),
         "shl_launch_count": (ctypes.c_longlong, []),
@@ -194,6 +195,12 @@ def shl_decompose_masked(h, f_masked, mask, f_est, batch, coeffs, dtype, ws, str
 def shl_reconstruct(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
     _check("shl_reconstruct", lib().shl_reconstruct(
         h, _ptr(coeffs), dtype, batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
+        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+
+
+def shl_shrink(h, x, mask, f_est, batch, thresh, x_out, ws, stream=None):
+    _check("shl_shrink", lib().shl_shrink(
+        h, _ptr(x), _ptr(mask), _ptr(f_est), batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
         ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
 
 
@@ -329,6 +336,27 @@ class Bank:
 
     def adjoint(self, c, thresh=None, out=None, ws=None):
         return self._rec(shl_adjoint, c, thresh, out, ws)
+
+    def shrink(self, x, thresh, mask_u8=None, f_est=None, out=None, ws=None):
+        """rec(T_thresh(dec(u))), u = x or mask (x - f_est) + f_est, without
+        storing coefficients (shl_shrink)."""
+        import torch
+        x = x.contiguous()
+        self._check_images(x)
+        B = x.shape[0]
+        thresh = thresh.to(device=x.device, dtype=torch.float32).contiguous()
+        if thresh.shape != (B, self.K):
+            raise ValueError("thresholds must be [B, K]")
+        if (mask_u8 is None) != (f_est is None):
+            raise ValueError("mask and f_est go together")
+        if mask_u8 is not None:
+            mask_u8 = mask_u8.contiguous()
+            f_est = f_est.contiguous()
+            self._check_images(f_est)
+        y = out if out is not None else torch.empty_like(x)
+        ws = ws if ws is not None else self.workspace(SHL_OP_SHRINK, B)
+        shl_shrink(self.handle, x, mask_u8, f_est, B, thresh, y, ws)
+        return y
 
     def subband_absmax(self, c, by_rms=False, out=None):
         import torch
