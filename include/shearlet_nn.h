@@ -41,6 +41,26 @@ shl_status shl_nn_conv3x3_backward_weight(const float* in, const float* gout, fl
                                           int B, int Ci, int Co, int H, int W, float* ws,
                                           void* stream);
 
+/* The same 3x3 convolution on the tensor cores (tcgen05): bfloat16 operands
+ * (inputs and weights rounded to nearest even), float32 accumulation, so
+ * the result equals the convolution of the bfloat16-rounded tensors up to
+ * float32 summation order.  Supported when shl_nn_conv3x3_tc_supported()
+ * (1 <= Ci, Co <= 48 and W a multiple of 128) and the input (gout for the
+ * backward call) is 16-byte aligned; SHL_EINVAL otherwise. */
+int shl_nn_conv3x3_tc_supported(int Ci, int Co, int H, int W);
+shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const float* bias,
+                                     float* out, int B, int Ci, int Co, int H, int W,
+                                     void* stream);
+/* gin for the convolution with w [Co][Ci][3][3] (flipped, channel-transposed
+ * weights), on the tensor cores; no workspace. */
+shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, float* gin, int B,
+                                           int Ci, int Co, int H, int W, void* stream);
+/* Synchronises `stream`, then reports SHL_ETIMEOUT if a tensor-core
+ * convolution on this device gave up waiting for its MMAs (bounded wait)
+ * since the last call, clearing the flag. */
+shl_status shl_nn_tc_status(void* stream);
+const char* shl_nn_tc_last_error(void);
+
 /* PReLU A(x) = x (x >= 0), a x (x < 0) with one slope a[0] per layer
  * (Sec. 4.4 writes the negative branch as -c x, i.e. a = -c). */
 shl_status shl_nn_prelu_forward(const float* x, const float* a, float* y, long long n, void* stream);

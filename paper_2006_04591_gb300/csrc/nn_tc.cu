@@ -1,0 +1,354 @@
+// nn_tc.cu - 3x3 convolutions of the learned parts on the tensor cores
+// (tcgen05, bfloat16 operands, float32 accumulation in tensor memory).
+//
+// Implicit GEMM per tile of 128 consecutive output pixels of one image row:
+//   D[m][n] = sum_{tap, ci} P_tap[m][ci] * W_tap[n][ci]
+// with P_tap[m][ci] = in[ci][y + dy - 1][x0 + m + dx - 1] (zero padding).
+// The CTA stages the three input rows it needs once, as bfloat16, in the
+// no-swizzle K-major core-matrix layout [row][ci/8][pixel][8 ci] (16 bytes
+// per pixel and channel group), loading float4 groups of 4 pixels.  Consecutive pixels are 16 bytes apart, so
+// the A operand of tap (dy, dx) is the same staged rows with its start
+// address moved by dx * 16 bytes: no im2col copy.  The weights sit in the
+// same layout [tap][ci/8][n][8 ci] for the whole launch.  One thread issues
+// the 9 * Ci/16 MMAs (M = 128, N = Cout padded to 16, K = 16) into a TMEM
+// accumulator and commits them to an mbarrier; the four warps then read
+// their 32 TMEM lanes (= pixels) and store the NCHW output rows.  The wait
+// on the mbarrier is bounded: when it runs out the kernel records the
+// error (read by shl_nn_tc_status), frees its TMEM and returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "../../include/shearlet_nn.h"
+
+namespace {
+
+__device__ unsigned int g_tc_err = 0;
+
+constexpr int TC_M = 128;            // output pixels per tile (MMA M)
+constexpr int TC_THREADS = 128;      // four warps: one per 32 TMEM lanes
+// Staged pixels per row: x0 - 4 .. x0 + 131, in float4 groups aligned to 16
+// bytes (x0 and W are multiples of 128, so each group lies wholly inside or
+// wholly outside the image); output pixel m, tap dx reads staged pixel
+// m + dx + 3.
+constexpr int PW = TC_M + 8;
+constexpr int PX0 = 3;
+constexpr unsigned TC_SPIN_LIMIT = 1u << 22;
+
+struct ConvTcArgs {
+  const float* in;      // [B][Cin][H][W]
+  const float* w;       // forward: [Cout][Cin][3][3]; flip: [Cin][Cout][3][3]
+  const float* bias;    // [Cout] or null
+  float* out;           // [B][Cout][H][W]
+  int B, Cin, Cout, H, W;
+  int flip;             // 1: convolution with the flipped, channel-transposed weights
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// Shared-memory matrix descriptor of tcgen05, no swizzle: start address,
+// leading-dimension byte offset (between core matrices along K), stride
+// byte offset (between 8-row groups along M or N), descriptor version 1.
+__device__ __forceinline__ uint64_t mdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  return d;
+}
+
+// Instruction descriptor of kind::f16: float32 accumulator, bfloat16 A and
+// B, both K-major, N and M.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ float wval(const ConvTcArgs& a, int n, int k, int dy, int dx) {
+  // n: output channel, k: input channel of this convolution
+  return a.flip ? __ldg(a.w + (((size_t)k * a.Cout + n) * 3 + (2 - dy)) * 3 + (2 - dx))
+                : __ldg(a.w + (((size_t)n * a.Cin + k) * 3 + dy) * 3 + dx);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t addr, uint32_t parity) {
+  for (unsigned i = 0; i < TC_SPIN_LIMIT; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+#define SHL_TMEM_LD16(R, ADDR)                                                              \
+  asm volatile(                                                                             \
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "                                             \
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"                     \
+      : "=r"((R)[0]), "=r"((R)[1]), "=r"((R)[2]), "=r"((R)[3]), "=r"((R)[4]), "=r"((R)[5]), \
+        "=r"((R)[6]), "=r"((R)[7]), "=r"((R)[8]), "=r"((R)[9]), "=r"((R)[10]),              \
+        "=r"((R)[11]), "=r"((R)[12]), "=r"((R)[13]), "=r"((R)[14]), "=r"((R)[15])           \
+      : "r"(ADDR)                                                                           \
+      : "memory")
+
+template <int CG, int NP>
+struct ConvTcT {
+  static_assert(CG % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 64, "tile shape");
+  static constexpr int KS = CG / 2;                          // K steps of 16 per tap
+  static constexpr size_t WBYTES = (size_t)9 * CG * NP * 16;  // [tap][cg][n][8]
+  static constexpr size_t PBYTES = (size_t)3 * CG * PW * 16;  // [row][cg][px][8]
+  static constexpr size_t SMEM = WBYTES + PBYTES;            // descriptors stay inside
+  static constexpr uint32_t NCOLS = NP <= 32 ? 32 : 64;       // TMEM columns (power of 2)
+};
+
+template <int CG, int NP>
+__global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
+  using P = ConvTcT<CG, NP>;
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* wsm = sm;
+  uint8_t* patch = sm + P::WBYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // weights -> bfloat16 [tap][cg][n][8], zero beyond Cin / Cout
+  for (int idx = tid; idx < 9 * CG * NP; idx += TC_THREADS) {
+    const int t = idx / (CG * NP), rem = idx - t * CG * NP, cg = rem / NP, n = rem - cg * NP;
+    const int dy = t / 3, dx = t - dy * 3;
+    uint32_t pk[4];
+#pragma unroll
+    for (int c = 0; c < 8; c += 2) {
+      const int k0 = cg * 8 + c;
+      const float v0 = (n < a.Cout && k0 < a.Cin) ? wval(a, n, k0, dy, dx) : 0.f;
+      const float v1 = (n < a.Cout && k0 + 1 < a.Cin) ? wval(a, n, k0 + 1, dy, dx) : 0.f;
+      pk[c / 2] = pack_bf16(v0, v1);
+    }
+    *reinterpret_cast<uint4*>(wsm + (size_t)idx * 16) = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(P::NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights -> async proxy
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(TC_M, NP);
+  const uint32_t wbase = smem_u32(wsm), pbase = smem_u32(patch);
+
+  const int tiles_x = a.W / TC_M;
+  const int ntiles = a.B * a.H * tiles_x;
+  uint32_t phase = 0;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int b = tile / (a.H * tiles_x), rem = tile - b * a.H * tiles_x;
+    const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * TC_M;
+    // input rows y-1..y+1, pixels x0-4..x0+131 -> bfloat16 [row][cg][px][8],
+    // one item = 4 pixels x 8 channels (8 float4 loads, 4 16-byte stores)
+    constexpr int PG = PW / 4;
+    const size_t cs = (size_t)a.H * a.W;
+    for (int idx = tid; idx < 3 * CG * PG; idx += TC_THREADS) {
+      const int r = idx / (CG * PG), rem2 = idx - r * CG * PG, cg = rem2 / PG, q = rem2 - cg * PG;
+      const int gy = y - 1 + r, gx = x0 - 4 + 4 * q;
+      const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+      const float* src = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W + (ok ? gx : 0);
+      float4 v[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c)
+        v[c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
+                                          : make_float4(0.f, 0.f, 0.f, 0.f);
+      uint8_t* dst = patch + ((size_t)(r * CG + cg) * PW + 4 * q) * 16;
+      *reinterpret_cast<uint4*>(dst) =
+          make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x),
+                     pack_bf16(v[4].x, v[5].x), pack_bf16(v[6].x, v[7].x));
+      *reinterpret_cast<uint4*>(dst + 16) =
+          make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y),
+                     pack_bf16(v[4].y, v[5].y), pack_bf16(v[6].y, v[7].y));
+      *reinterpret_cast<uint4*>(dst + 32) =
+          make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z),
+                     pack_bf16(v[4].z, v[5].z), pack_bf16(v[6].z, v[7].z));
+      *reinterpret_cast<uint4*>(dst + 48) =
+          make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w),
+                     pack_bf16(v[4].w, v[5].w), pack_bf16(v[6].w, v[7].w));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // patch -> async proxy
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int t = 0; t < 9; ++t) {
+        const int dy = t / 3, dx = t - dy * 3;
+#pragma unroll
+        for (int s = 0; s < P::KS; ++s) {
+          const uint64_t ad = mdesc(pbase + (uint32_t)(((dy * CG + 2 * s) * PW + dx + PX0) * 16),
+                                    PW * 16, 128);
+          const uint64_t bd = mdesc(wbase + (uint32_t)(((t * CG + 2 * s) * NP) * 16), NP * 16, 128);
+          const uint32_t acc = (t | s) != 0;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar))
+          : "memory");
+    }
+    if (!mbar_wait(smem_u32(&mbar), phase)) {
+      atomicOr(&g_tc_err, 1u);
+      s_fail = 1;
+    }
+    phase ^= 1u;
+    __syncthreads();
+    if (s_fail) break;
+    tc_fence_after();
+    uint32_t acc[NP];
+#pragma unroll
+    for (int q = 0; q < NP / 16; ++q)
+      SHL_TMEM_LD16(acc + 16 * q, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    const int x = x0 + warp * 32 + lane;
+    float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x;
+#pragma unroll
+    for (int n = 0; n < NP; ++n) {
+      if (n < a.Cout) o[n * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + n) : 0.f);
+    }
+    tc_fence_before();
+    __syncthreads();   // TMEM accumulator and patch free for the next tile
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(P::NCOLS)
+                 : "memory");
+}
+
+template <int CG, int NP>
+cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
+  using P = ConvTcT<CG, NP>;
+  auto k = k_conv3x3_tc<CG, NP>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+  if (e) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC_THREADS, P::SMEM))) return e;
+  // TMEM: at most 512 columns per SM between the resident CTAs
+  per_sm = std::max(1, std::min(per_sm, (int)(512 / P::NCOLS)));
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int ntiles = a.B * a.H * (a.W / TC_M);
+  const int grid = std::max(1, std::min(ntiles, per_sm * std::max(sms, 1)));
+  k<<<grid, TC_THREADS, P::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
+int round16(int v) { return (v + 15) / 16 * 16; }
+
+cudaError_t dispatch(const ConvTcArgs& a, cudaStream_t st) {
+  const int cg = round16(a.Cin) / 8, np = round16(a.Cout);
+#define SHL_TC(CGV, NPV) \
+  if (cg == CGV && np == NPV) return launch_tc<CGV, NPV>(a, st);
+  SHL_TC(2, 16) SHL_TC(2, 32) SHL_TC(2, 48)
+  SHL_TC(4, 16) SHL_TC(4, 32) SHL_TC(4, 48)
+  SHL_TC(6, 16) SHL_TC(6, 32) SHL_TC(6, 48)
+#undef SHL_TC
+  return cudaErrorInvalidValue;
+}
+
+thread_local const char* g_tc_msg = "";
+
+shl_status tc_run(const ConvTcArgs& a, void* stream, const char* where) {
+  if (a.B == 0) return SHL_OK;
+  cudaError_t e = dispatch(a, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    g_tc_msg = where;
+    return SHL_ECUDA;
+  }
+  return SHL_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int shl_nn_conv3x3_tc_supported(int Ci, int Co, int H, int W) {
+  return Ci >= 1 && Ci <= 48 && Co >= 1 && Co <= 48 && H >= 1 && W >= TC_M && W % TC_M == 0;
+}
+
+shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const float* bias,
+                                     float* out, int B, int Ci, int Co, int H, int W,
+                                     void* stream) {
+  if (!in || !w || !out || B < 0 || !shl_nn_conv3x3_tc_supported(Ci, Co, H, W) ||
+      (reinterpret_cast<uintptr_t>(in) & 15u)) {
+    g_tc_msg = "conv3x3_forward_tc: bad arguments, unsupported shape or input not 16-byte aligned";
+    return SHL_EINVAL;
+  }
+  const ConvTcArgs a{in, w, bias, out, B, Ci, Co, H, W, 0};
+  return tc_run(a, stream, "conv3x3_forward_tc: launch failed");
+}
+
+shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, float* gin, int B,
+                                           int Ci, int Co, int H, int W, void* stream) {
+  if (!gout || !w || !gin || B < 0 || !shl_nn_conv3x3_tc_supported(Co, Ci, H, W) ||
+      (reinterpret_cast<uintptr_t>(gout) & 15u)) {
+    g_tc_msg = "conv3x3_backward_data_tc: bad arguments, unsupported shape or gout not 16-byte aligned";
+    return SHL_EINVAL;
+  }
+  // gin = conv(gout, flipped and channel-transposed w): Cin = Co, Cout = Ci
+  const ConvTcArgs a{gout, w, nullptr, gin, B, Co, Ci, H, W, 1};
+  return tc_run(a, stream, "conv3x3_backward_data_tc: launch failed");
+}
+
+shl_status shl_nn_tc_status(void* stream) {
+  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
+    g_tc_msg = "shl_nn_tc_status: stream synchronisation failed";
+    return SHL_ECUDA;
+  }
+  unsigned flag = 0;
+  if (cudaMemcpyFromSymbol(&flag, g_tc_err, sizeof(flag)) != cudaSuccess) return SHL_ECUDA;
+  if (flag) {
+    const unsigned zero = 0;
+    cudaMemcpyToSymbol(g_tc_err, &zero, sizeof(zero));
+    g_tc_msg = "a tensor-core convolution gave up waiting for its MMAs";
+    return SHL_ETIMEOUT;
+  }
+  return SHL_OK;
+}
+
+const char* shl_nn_tc_last_error(void) { return g_tc_msg; }
+
+}  // extern "C"

@@ -241,14 +241,15 @@ def coeff_net_step(bank: Bank, net, opt, x_noisy, clean):
     return loss
 
 
-def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3):
-    """Training-step time of the coefficient network (bfloat16 coefficients)."""
+def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3, tc=True):
+    """Training-step time of the coefficient network (bfloat16 coefficients;
+    tc: tensor-core convolutions for the forward and input gradients)."""
     bank = Bank.create(N, N, scales, device=0)
     dev = torch.device("cuda", 0)
     clean, noisy = synth.denoise_batch(B, N, 30 / 255, seed0=1000)
     x = torch.from_numpy(noisy.astype(np.float32)).to(dev)
     y = torch.from_numpy(clean.astype(np.float32)).to(dev)
-    net = nn.CoeffNet(bank.K, ch=32, seed=0, device=dev)
+    net = nn.CoeffNet(bank.K, ch=32, seed=0, device=dev, tc=tc)
     opt = nn.Adam(list(net.parameters()), lr=1e-3)
     losses = []
     for _ in range(warmup):
@@ -265,6 +266,7 @@ def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3):
     ms = a.elapsed_time(b) / steps
     conv_flops = 2 * B * N * N * 9 * (bank.K * 32 + 32 * 32 + 32 * bank.K) * 3   # fwd + 2 bwd
     return {"batch": B, "size": N, "filters": bank.K, "coeff_dtype": "bf16",
+            "conv": "tcgen05 bf16 (fwd, input grad) + float32 (weight grad)" if tc else "float32",
             "ms_per_train_step": ms, "conv_tflops": conv_flops / (ms / 1e3) / 1e12,
             "loss_first": losses[0], "loss_last": losses[-1]}
 

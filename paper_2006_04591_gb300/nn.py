@@ -9,6 +9,10 @@ networks and Adam.
 * CoeffNet - residual 3-layer CNN on shearlet coefficients after the learned
   proximal operators of Sec. 4.4: c + W3 A W2 A W1 c, PReLU A.
 
+Both networks run their 3x3 convolutions (forward and input gradient) on the
+tensor cores (tcgen05, bfloat16 operands, float32 accumulation) wherever the
+shape allows it (tc=True, the default), else on the float32 kernels.
+
 torch only provides tensors (memory), parameter containers and the autograd
 tape; every arithmetic step calls the library.
 """
@@ -36,6 +40,11 @@ def lib():
             "shl_nn_conv3x3_workspace_floats": (sz, [i, i, i, i, i]),
             "shl_nn_conv3x3_backward_data": (i, [vp, vp, vp, i, i, i, i, i, vp, vp]),
             "shl_nn_conv3x3_backward_weight": (i, [vp, vp, vp, vp, i, i, i, i, i, vp, vp]),
+            "shl_nn_conv3x3_tc_supported": (i, [i, i, i, i]),
+            "shl_nn_conv3x3_forward_tc": (i, [vp, vp, vp, vp, i, i, i, i, i, vp]),
+            "shl_nn_conv3x3_backward_data_tc": (i, [vp, vp, vp, i, i, i, i, i, vp]),
+            "shl_nn_tc_status": (i, [vp]),
+            "shl_nn_tc_last_error": (ctypes.c_char_p, []),
             "shl_nn_prelu_forward": (i, [vp, vp, vp, ll, vp]),
             "shl_nn_reduce_workspace_floats": (sz, [ll]),
             "shl_nn_prelu_backward": (i, [vp, vp, vp, vp, vp, ll, vp, vp]),
@@ -90,7 +99,33 @@ def shl_nn_conv3x3_forward(x, w, b, out):
                                                           w.shape[0], H, W, _st(x)))
 
 
-def shl_nn_conv3x3_backward(x, w, gout, need_gin=True):
+def _chk_tc(name, st):
+    if st != 0:
+        raise S.ShearletError(name, st, lib().shl_nn_tc_last_error().decode())
+
+
+def shl_nn_conv3x3_tc_supported(Ci, Co, H, W):
+    return bool(lib().shl_nn_conv3x3_tc_supported(Ci, Co, H, W))
+
+
+def shl_nn_conv3x3_forward_tc(x, w, b, out):
+    B, Ci, H, W = x.shape
+    _chk_tc("conv3x3_forward_tc", lib().shl_nn_conv3x3_forward_tc(
+        _p(x), _p(w), _p(b), _p(out), B, Ci, w.shape[0], H, W, _st(x)))
+
+
+def shl_nn_conv3x3_backward_data_tc(gout, w, gin):
+    B, Ci, H, W = gin.shape
+    _chk_tc("conv3x3_backward_data_tc", lib().shl_nn_conv3x3_backward_data_tc(
+        _p(gout), _p(w), _p(gin), B, Ci, w.shape[0], H, W, _st(gin)))
+
+
+def shl_nn_tc_status(stream=None):
+    s = ctypes.c_void_p(None if stream is None else stream.cuda_stream)
+    _chk_tc("tc_status", lib().shl_nn_tc_status(s))
+
+
+def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False):
     B, Ci, H, W = x.shape
     Co = w.shape[0]
     L = lib()
@@ -102,19 +137,30 @@ def shl_nn_conv3x3_backward(x, w, gout, need_gin=True):
     gin = None
     if need_gin:
         gin = torch.empty_like(x)
-        _chk("conv3x3_backward_data", L.shl_nn_conv3x3_backward_data(
-            _p(gout), _p(w), _p(gin), B, Ci, Co, H, W, _p(ws), _st(x)))
+        if tc:
+            shl_nn_conv3x3_backward_data_tc(gout, w, gin)
+        else:
+            _chk("conv3x3_backward_data", L.shl_nn_conv3x3_backward_data(
+                _p(gout), _p(w), _p(gin), B, Ci, Co, H, W, _p(ws), _st(x)))
     return gin, gw, gb
 
 
 # ------------------------------------------------------------- autograd
 class _Conv3x3(torch.autograd.Function):
     @staticmethod
-    def forward(ctx, x, w, b):
+    def forward(ctx, x, w, b, tc):
         x = x.contiguous()
         out = torch.empty((x.shape[0], w.shape[0], x.shape[2], x.shape[3]), dtype=torch.float32,
                           device=x.device)
-        shl_nn_conv3x3_forward(x, w.contiguous(), b.contiguous(), out)
+        B, Ci, H, W = x.shape
+        Co = w.shape[0]
+        # tensor cores for the forward and the input gradient where the shape allows
+        ctx.tc_fwd = bool(tc) and shl_nn_conv3x3_tc_supported(Ci, Co, H, W)
+        ctx.tc_bwd = bool(tc) and shl_nn_conv3x3_tc_supported(Co, Ci, H, W)
+        if ctx.tc_fwd:
+            shl_nn_conv3x3_forward_tc(x, w.contiguous(), b.contiguous(), out)
+        else:
+            shl_nn_conv3x3_forward(x, w.contiguous(), b.contiguous(), out)
         ctx.save_for_backward(x, w)
         return out
 
@@ -122,8 +168,8 @@ class _Conv3x3(torch.autograd.Function):
     def backward(ctx, gout):
         x, w = ctx.saved_tensors
         gin, gw, gb = shl_nn_conv3x3_backward(x, w.contiguous(), gout.contiguous(),
-                                             ctx.needs_input_grad[0])
-        return gin, gw, gb
+                                             ctx.needs_input_grad[0], tc=ctx.tc_bwd)
+        return gin, gw, gb, None
 
 
 class _PReLU(torch.autograd.Function):
@@ -273,8 +319,11 @@ class _MSE(torch.autograd.Function):
         return ga, None
 
 
-def conv3x3(x, w, b):
-    return _Conv3x3.apply(x, w, b)
+def conv3x3(x, w, b, tc=False):
+    """3x3 convolution; tc=True runs the forward and the input gradient on
+    the tensor cores (bfloat16 operands, float32 accumulation) when
+    shl_nn_conv3x3_tc_supported, else the float32 kernels."""
+    return _Conv3x3.apply(x, w, b, tc)
 
 
 def prelu(x, a):
@@ -352,10 +401,10 @@ def _init_conv(co, ci, gen, device):
 class ThresholdNet(torch.nn.Module):
     """[B, 2, H, W] (f_masked, mask) -> thresholds [B, T, K] (relative to RMS_i)."""
 
-    def __init__(self, K, T=10, ch=32, pool=4, seed=0, device="cuda", scale=1.0):
+    def __init__(self, K, T=10, ch=32, pool=4, seed=0, device="cuda", scale=1.0, tc=True):
         super().__init__()
         g = torch.Generator().manual_seed(seed)
-        self.K, self.T, self.pool = K, T, pool
+        self.K, self.T, self.pool, self.tc = K, T, pool, tc
         chans = [2, ch, ch, ch, ch]
         for l in range(4):
             w, b = _init_conv(chans[l + 1], chans[l], g, device)
@@ -368,7 +417,7 @@ class ThresholdNet(torch.nn.Module):
     def forward(self, x):
         h = avgpool(x, self.pool) if self.pool > 1 else x
         for l in range(4):
-            h = prelu(conv3x3(h, getattr(self, "w%d" % l), getattr(self, "b%d" % l)),
+            h = prelu(conv3x3(h, getattr(self, "w%d" % l), getattr(self, "b%d" % l), self.tc),
                       getattr(self, "a%d" % l))
         y = softplus(linear(gap(h), self.wl, self.bl))
         return y.reshape(x.shape[0], self.T, self.K)
@@ -377,9 +426,10 @@ class ThresholdNet(torch.nn.Module):
 class CoeffNet(torch.nn.Module):
     """c + W3 A W2 A W1 c on [B, K, H, W] float32 coefficients."""
 
-    def __init__(self, K, ch=32, seed=0, device="cuda"):
+    def __init__(self, K, ch=32, seed=0, device="cuda", tc=True):
         super().__init__()
         g = torch.Generator().manual_seed(seed)
+        self.tc = tc
         chans = [K, ch, ch, K]
         for l in range(3):
             w, b = _init_conv(chans[l + 1], chans[l], g, device)
@@ -391,9 +441,9 @@ class CoeffNet(torch.nn.Module):
         self.a1 = torch.nn.Parameter(torch.full((1,), 0.25, device=device))
 
     def forward(self, c):
-        h = prelu(conv3x3(c, self.w0, self.b0), self.a0)
-        h = prelu(conv3x3(h, self.w1, self.b1), self.a1)
-        return c + conv3x3(h, self.w2, self.b2)
+        h = prelu(conv3x3(c, self.w0, self.b0, self.tc), self.a0)
+        h = prelu(conv3x3(h, self.w1, self.b1, self.tc), self.a1)
+        return c + conv3x3(h, self.w2, self.b2, self.tc)
 
 
 class Adam:

@@ -1,0 +1,113 @@
+"""Tensor-core (tcgen05) 3x3 convolutions: the kernel rounds inputs and
+weights to bfloat16 (nearest even) and accumulates in float32, so it must
+equal the float64 oracle convolution of the bfloat16-rounded tensors up to
+float32 summation error; the input gradient likewise with the rounded
+output gradient and weights."""
+
+import numpy as np
+import pytest
+
+from oracle import nn as ON
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 2e-5
+
+
+def _rel(a, b):
+    a = a.detach().double().cpu()
+    b = b.detach().double().cpu()
+    return ((a - b).abs().max() / b.abs().max().clamp_min(1e-30)).item()
+
+
+def _bf(t):
+    return t.to(torch.bfloat16).double()
+
+
+SHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 16, 16, 3, 384),
+          (1, 48, 48, 2, 128), (3, 32, 32, 1, 128), (1, 7, 5, 6, 256)]
+
+
+@pytest.mark.parametrize("B,Ci,Co,H,W", SHAPES)
+def test_tc_forward_matches_rounded_oracle(B, Ci, Co, H, W):
+    from paper_2006_04591_gb300 import nn
+    assert nn.shl_nn_conv3x3_tc_supported(Ci, Co, H, W)
+    gen = torch.Generator().manual_seed(B * 1000 + Ci * 10 + Co)
+    x = torch.randn((B, Ci, H, W), generator=gen)
+    w = torch.randn((Co, Ci, 3, 3), generator=gen) * 0.2
+    b = torch.randn(Co, generator=gen)
+    out = torch.empty((B, Co, H, W), device="cuda")
+    nn.shl_nn_conv3x3_forward_tc(x.cuda(), w.cuda(), b.cuda(), out)
+    nn.shl_nn_tc_status()
+    want = ON.conv3x3(_bf(x), _bf(w), b.double())
+    assert _rel(out, want) <= TOL
+
+
+@pytest.mark.parametrize("B,Ci,Co,H,W", SHAPES)
+def test_tc_backward_data_matches_rounded_oracle(B, Ci, Co, H, W):
+    from paper_2006_04591_gb300 import nn
+    gen = torch.Generator().manual_seed(B * 7 + Ci + Co * 3)
+    w = torch.randn((Co, Ci, 3, 3), generator=gen) * 0.2
+    gout = torch.randn((B, Co, H, W), generator=gen)
+    gin = torch.empty((B, Ci, H, W), device="cuda")
+    nn.shl_nn_conv3x3_backward_data_tc(gout.cuda(), w.cuda(), gin)
+    nn.shl_nn_tc_status()
+    xo = torch.zeros((B, Ci, H, W), dtype=torch.float64, requires_grad=True)
+    yo = ON.conv3x3(xo, _bf(w), torch.zeros(Co, dtype=torch.float64))
+    (yo * _bf(gout)).sum().backward()
+    assert _rel(gin, xo.grad) <= TOL
+
+
+def test_tc_rejects_unsupported_shapes():
+    from paper_2006_04591_gb300 import nn
+    from paper_2006_04591_gb300.shearlet import ShearletError
+    assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 100)
+    assert not nn.shl_nn_conv3x3_tc_supported(64, 32, 8, 128)
+    x = torch.zeros((1, 32, 8, 100), device="cuda")
+    with pytest.raises(ShearletError):
+        nn.shl_nn_conv3x3_forward_tc(x, torch.zeros((32, 32, 3, 3), device="cuda"), None,
+                                     torch.empty_like(x))
+
+
+class _RoundedConv(torch.autograd.Function):
+    """float64 reference of what the tensor-core path computes: the forward
+    and the input gradient see bfloat16-rounded operands, the weight gradient
+    (float32 kernel on the GPU) the unrounded ones."""
+
+    @staticmethod
+    def forward(ctx, x, w, b):
+        ctx.save_for_backward(x, w)
+        return ON.conv3x3(_bf(x), _bf(w), b)
+
+    @staticmethod
+    def backward(ctx, g):
+        x, w = ctx.saved_tensors
+        F = torch.nn.grad
+        gin = F.conv2d_input(x.shape, _bf(w), _bf(g), padding=1)
+        gw = F.conv2d_weight(x, w.shape, g, padding=1)
+        return gin, gw, g.sum((0, 2, 3))
+
+
+def test_coeff_net_tc_matches_rounded_reference():
+    """The residual coefficient network with tensor-core convolutions against
+    a float64 network that rounds the same operands to bfloat16: output and
+    first-layer weight gradient agree to float32 level (the bfloat16 rounding
+    itself moves that gradient by ~2 % relative L2 here, so a comparison with
+    the float32 path could not tell a layout error from rounding)."""
+    from paper_2006_04591_gb300 import nn
+    c = torch.randn((2, 33, 8, 128), generator=torch.Generator().manual_seed(9))
+    net = nn.CoeffNet(K=33, ch=32, seed=5, tc=True)
+    y = net(c.cuda())
+    (y * y).sum().backward()
+    nn.shl_nn_tc_status()
+    P = {k: v.detach().double().cpu() for k, v in net.named_parameters()}
+    w0 = P["w0"].clone().requires_grad_(True)
+    pr = lambda h, a: torch.where(h >= 0, h, a * h)
+    h = pr(_RoundedConv.apply(c.double(), w0, P["b0"]), P["a0"])
+    h = pr(_RoundedConv.apply(h, P["w1"], P["b1"]), P["a1"])
+    yo = c.double() + _RoundedConv.apply(h, P["w2"], P["b2"])
+    (yo * yo).sum().backward()
+    l2 = lambda a, b: ((a.detach().double().cpu() - b).norm() / b.norm()).item()
+    assert l2(y, yo) <= 1e-4
+    assert l2(net.w0.grad, w0.grad) <= 1e-3
