@@ -55,6 +55,18 @@ shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const floa
  * weights), on the tensor cores; no workspace. */
 shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, float* gin, int B,
                                            int Ci, int Co, int H, int W, void* stream);
+/* Weight (and bias) gradient on the tensor cores: gw = sum over pixels of
+ * gout x shifted input with both rounded to bfloat16, float32 accumulation
+ * (per-CTA partials in ws, summed in a fixed order); gb (may be NULL) in
+ * float32 from the unrounded gout.  Supported when
+ * shl_nn_conv3x3_wgrad_tc_supported() (3 Ci <= 128, Co <= 48, W a multiple
+ * of 128) and in, gout are 16-byte aligned; ws holds
+ * shl_nn_conv3x3_backward_weight_tc_workspace_floats() floats. */
+int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W);
+size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W);
+shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout, float* gw,
+                                             float* gb, int B, int Ci, int Co, int H, int W,
+                                             float* ws, void* stream);
 /* Synchronises `stream`, then reports SHL_ETIMEOUT if a tensor-core
  * convolution on this device gave up waiting for its MMAs (bounded wait)
  * since the last call, clearing the flag. */

@@ -256,6 +256,225 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
                  : "memory");
 }
 
+// ----------------------------------------------------------- weight gradient
+// gw[o][i][dy][dx] = sum_{b,y,x} gout[b][o][y][x] in[b][i][y+dy-1][x+dx-1].
+// Per unit of 128 consecutive pixels of one row (K = pixels, 16 per MMA):
+//   A_dy[r][p] = in[i][y+dy-1][x0+p+dx-1], r = dx * Cin + i  (3 Cin <= 128 rows)
+//   B[o][p]    = gout[o][y][x0+p]                             (NP rows)
+//   D_dy[r][o] += sum_p A_dy[r][p] B[o][p]                    (TMEM columns dy * NP + o)
+// both staged as bfloat16 K-major core matrices [pixel/8][row][8 pixels].
+// A CTA accumulates all its units in TMEM and writes one partial
+// gw[o][i][dy][dx]; k_wgrad_reduce sums the partials in CTA order.
+struct WgradTcArgs {
+  const float* in;      // [B][Cin][H][W]
+  const float* gout;    // [B][Cout][H][W]
+  float* part;          // [gridDim.x][Cout][Cin][9]
+  int B, Cin, Cout, H, W;
+};
+
+template <int NP>
+struct WgradTcT {
+  static constexpr int PG = TC_M / 8;                       // pixel groups per unit
+  static constexpr size_t ABYTES = (size_t)PG * 128 * 16;   // one dy: [pg][r][8]
+  static constexpr size_t BBYTES = (size_t)PG * NP * 16;    // [pg][o][8]
+  static constexpr size_t SMEM = 3 * ABYTES + BBYTES;
+  static constexpr uint32_t NCOLS = 3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : 256);
+};
+
+template <int NP>
+__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
+  using P = WgradTcT<NP>;
+  extern __shared__ __align__(128) uint8_t sm[];
+  uint8_t* As = sm;                       // 3 x [pg][128][8]
+  uint8_t* Bs = sm + 3 * P::ABYTES;       // [pg][NP][8]
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // rows r >= 3 Cin and o >= Cout stay zero for the whole launch
+  for (size_t q = tid; q < P::SMEM / 16; q += TC_THREADS)
+    reinterpret_cast<uint4*>(sm)[q] = make_uint4(0u, 0u, 0u, 0u);
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(&tmem_slot)),
+                 "r"(P::NCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&mbar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+  const uint32_t idesc = idesc_bf16(TC_M, NP);
+  const uint32_t abase = smem_u32(As), bbase = smem_u32(Bs);
+  const int tiles_x = a.W / TC_M;
+  const int nunits = a.B * a.H * tiles_x;
+  uint32_t phase = 0;
+  bool first = true;
+  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
+    const int b = u / (a.H * tiles_x), rem = u - b * a.H * tiles_x;
+    const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * TC_M;
+    // B: gout rows, 8 pixels per item
+    for (int idx = tid; idx < a.Cout * P::PG; idx += TC_THREADS) {
+      const int o = idx / P::PG, pg = idx - o * P::PG;
+      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
+      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
+      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+      *reinterpret_cast<uint4*>(Bs + ((size_t)pg * NP + o) * 16) =
+          make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
+                     pack_bf16(v1.z, v1.w));
+    }
+    // A: for each dy and input channel, 10 input pixels give the three
+    // shifted 8-pixel rows (dx = 0, 1, 2)
+    for (int idx = tid; idx < 3 * a.Cin * P::PG; idx += TC_THREADS) {
+      const int dy = idx / (a.Cin * P::PG), rem2 = idx - dy * a.Cin * P::PG;
+      const int i = rem2 / P::PG, pg = rem2 - i * P::PG;
+      const int gy = y + dy - 1, xs = x0 + 8 * pg;
+      float e[10];
+      if (gy >= 0 && gy < a.H) {
+        const float* src = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W + xs;
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+        e[0] = xs > 0 ? __ldg(src - 1) : 0.f;
+        e[1] = v0.x; e[2] = v0.y; e[3] = v0.z; e[4] = v0.w;
+        e[5] = v1.x; e[6] = v1.y; e[7] = v1.z; e[8] = v1.w;
+        e[9] = xs + 8 < a.W ? __ldg(src + 8) : 0.f;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 10; ++c) e[c] = 0.f;
+      }
+      uint8_t* dst = As + (size_t)dy * P::ABYTES + ((size_t)pg * 128 + i) * 16;
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx)   // pixel x0+8pg+j-1+dx = e[j + dx]
+        *reinterpret_cast<uint4*>(dst + (size_t)dx * a.Cin * 16) =
+            make_uint4(pack_bf16(e[dx], e[dx + 1]), pack_bf16(e[dx + 2], e[dx + 3]),
+                       pack_bf16(e[dx + 4], e[dx + 5]), pack_bf16(e[dx + 6], e[dx + 7]));
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy) {
+#pragma unroll
+        for (int s = 0; s < P::PG / 2; ++s) {
+          const uint64_t ad = mdesc(abase + (uint32_t)(dy * P::ABYTES + (size_t)2 * s * 128 * 16),
+                                    128 * 16, 128);
+          const uint64_t bd = mdesc(bbase + (uint32_t)(2 * s * NP * 16), NP * 16, 128);
+          const uint32_t acc = (first && s == 0) ? 0u : 1u;
+          asm volatile(
+              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                  tmem + (uint32_t)(dy * NP)),
+              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+              : "memory");
+        }
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              smem_u32(&mbar))
+          : "memory");
+    }
+    first = false;
+    if (!mbar_wait(smem_u32(&mbar), phase)) {   // staging buffers are reused next unit
+      atomicOr(&g_tc_err, 1u);
+      s_fail = 1;
+    }
+    phase ^= 1u;
+    tc_fence_before();
+    __syncthreads();
+    if (s_fail) break;
+  }
+  // epilogue: lane r = dx * Cin + i of warp r / 32, columns dy * NP + o
+  if (!s_fail) {
+    tc_fence_after();
+    const int r = warp * 32 + lane;
+    const int dx = r / a.Cin, i = r - dx * a.Cin;
+    float* part = a.part + (size_t)blockIdx.x * a.Cout * a.Cin * 9;
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy) {
+      uint32_t acc[NP];
+#pragma unroll
+      for (int q = 0; q < NP / 16; ++q)
+        SHL_TMEM_LD16(acc + 16 * q,
+                      tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dy * NP + 16 * q));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (dx < 3) {
+#pragma unroll
+        for (int o = 0; o < NP; ++o)
+          if (o < a.Cout)
+            part[(((size_t)o * a.Cin + i) * 3 + dy) * 3 + dx] =
+                blockIdx.x < nunits ? __uint_as_float(acc[o]) : 0.f;
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(P::NCOLS)
+                 : "memory");
+}
+
+// gw[e] = sum_c part[c][e] in CTA order; gb[o] = sum over b, pixels of gout
+// (one CTA per channel, fixed thread mapping, tree reduction).
+__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ gw, int nparts,
+                               int n) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  float s = 0.f;
+  for (int c = 0; c < nparts; ++c) s += part[(size_t)c * n + e];
+  gw[e] = s;
+}
+
+__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ gout,
+                                                   float* __restrict__ gb, int B, int C,
+                                                   long long HW) {
+  const int o = blockIdx.x;
+  float s = 0.f;
+  for (int b = 0; b < B; ++b) {
+    const float* p = gout + ((size_t)b * C + o) * HW;
+    for (long long q = threadIdx.x; q < HW; q += blockDim.x) s += p[q];
+  }
+  __shared__ float red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) gb[o] = red[0];
+}
+
+int wgrad_grid(int B, int H, int W) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int nunits = B * H * (W / TC_M);
+  return std::max(1, std::min(nunits, 2 * std::max(sms, 1)));
+}
+
+template <int NP>
+cudaError_t launch_wgrad(const WgradTcArgs& a, int grid, cudaStream_t st) {
+  using P = WgradTcT<NP>;
+  auto k = k_wgrad_tc<NP>;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
+  if (e) return e;
+  int per_sm = 0;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC_THREADS, P::SMEM))) return e;
+  if (per_sm < 1 || per_sm * (int)P::NCOLS > 512) return cudaErrorInvalidConfiguration;
+  k<<<grid, TC_THREADS, P::SMEM, st>>>(a);
+  return cudaGetLastError();
+}
+
 template <int CG, int NP>
 cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   using P = ConvTcT<CG, NP>;
@@ -330,6 +549,43 @@ shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, fl
   // gin = conv(gout, flipped and channel-transposed w): Cin = Co, Cout = Ci
   const ConvTcArgs a{gout, w, nullptr, gin, B, Co, Ci, H, W, 1};
   return tc_run(a, stream, "conv3x3_backward_data_tc: launch failed");
+}
+
+int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W) {
+  return Ci >= 1 && 3 * Ci <= 128 && Co >= 1 && Co <= 48 && H >= 1 && W >= TC_M && W % TC_M == 0;
+}
+
+size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W) {
+  if (B < 1 || !shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)) return 0;
+  return (size_t)wgrad_grid(B, H, W) * Co * Ci * 9;
+}
+
+shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout, float* gw,
+                                             float* gb, int B, int Ci, int Co, int H, int W,
+                                             float* ws, void* stream) {
+  if (!in || !gout || !gw || !ws || B < 1 || !shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W) ||
+      ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(gout)) & 15u)) {
+    g_tc_msg = "conv3x3_backward_weight_tc: bad arguments, unsupported shape or misaligned input";
+    return SHL_EINVAL;
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int grid = wgrad_grid(B, H, W);
+  const WgradTcArgs a{in, gout, ws, B, Ci, Co, H, W};
+  const int np = round16(Co);
+  cudaError_t e = np == 16 ? launch_wgrad<16>(a, grid, st)
+                : np == 32 ? launch_wgrad<32>(a, grid, st)
+                           : launch_wgrad<48>(a, grid, st);
+  if (e == cudaSuccess) {
+    const int n = Co * Ci * 9;
+    k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(ws, gw, grid, n);
+    if (gb) k_bias_grad<<<Co, 256, 0, st>>>(gout, gb, B, Co, (long long)H * W);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    g_tc_msg = "conv3x3_backward_weight_tc: launch failed";
+    return SHL_ECUDA;
+  }
+  return SHL_OK;
 }
 
 shl_status shl_nn_tc_status(void* stream) {

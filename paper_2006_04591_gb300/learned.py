@@ -266,7 +266,7 @@ def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3, tc=True):
     ms = a.elapsed_time(b) / steps
     conv_flops = 2 * B * N * N * 9 * (bank.K * 32 + 32 * 32 + 32 * bank.K) * 3   # fwd + 2 bwd
     return {"batch": B, "size": N, "filters": bank.K, "coeff_dtype": "bf16",
-            "conv": "tcgen05 bf16 (fwd, input grad) + float32 (weight grad)" if tc else "float32",
+            "conv": "tcgen05 bf16 (forward, input and weight gradients)" if tc else "float32",
             "ms_per_train_step": ms, "conv_tflops": conv_flops / (ms / 1e3) / 1e12,
             "loss_first": losses[0], "loss_last": losses[-1]}
 

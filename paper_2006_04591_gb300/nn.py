@@ -9,8 +9,8 @@ networks and Adam.
 * CoeffNet - residual 3-layer CNN on shearlet coefficients after the learned
   proximal operators of Sec. 4.4: c + W3 A W2 A W1 c, PReLU A.
 
-Both networks run their 3x3 convolutions (forward and input gradient) on the
-tensor cores (tcgen05, bfloat16 operands, float32 accumulation) wherever the
+Both networks run their 3x3 convolutions (forward, input and weight
+gradients) on the tensor cores (tcgen05, bfloat16 operands, float32 accumulation) wherever the
 shape allows it (tc=True, the default), else on the float32 kernels.
 
 torch only provides tensors (memory), parameter containers and the autograd
@@ -44,6 +44,9 @@ def lib():
             "shl_nn_conv3x3_forward_tc": (i, [vp, vp, vp, vp, i, i, i, i, i, vp]),
             "shl_nn_conv3x3_backward_data_tc": (i, [vp, vp, vp, i, i, i, i, i, vp]),
             "shl_nn_tc_status": (i, [vp]),
+            "shl_nn_conv3x3_wgrad_tc_supported": (i, [i, i, i, i]),
+            "shl_nn_conv3x3_backward_weight_tc_workspace_floats": (sz, [i, i, i, i, i]),
+            "shl_nn_conv3x3_backward_weight_tc": (i, [vp, vp, vp, vp, i, i, i, i, i, vp, vp]),
             "shl_nn_tc_last_error": (ctypes.c_char_p, []),
             "shl_nn_prelu_forward": (i, [vp, vp, vp, ll, vp]),
             "shl_nn_reduce_workspace_floats": (sz, [ll]),
@@ -120,20 +123,37 @@ def shl_nn_conv3x3_backward_data_tc(gout, w, gin):
         _p(gout), _p(w), _p(gin), B, Ci, w.shape[0], H, W, _st(gin)))
 
 
+def shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W):
+    return bool(lib().shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W))
+
+
+def shl_nn_conv3x3_backward_weight_tc(x, gout, gw, gb):
+    B, Ci, H, W = x.shape
+    Co = gout.shape[1]
+    L = lib()
+    ws = _ws(L.shl_nn_conv3x3_backward_weight_tc_workspace_floats(B, Ci, Co, H, W), x)
+    _chk_tc("conv3x3_backward_weight_tc", L.shl_nn_conv3x3_backward_weight_tc(
+        _p(x), _p(gout), _p(gw), _p(gb), B, Ci, Co, H, W, _p(ws), _st(x)))
+
+
 def shl_nn_tc_status(stream=None):
     s = ctypes.c_void_p(None if stream is None else stream.cuda_stream)
     _chk_tc("tc_status", lib().shl_nn_tc_status(s))
 
 
-def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False):
+def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False, tc_w=False):
     B, Ci, H, W = x.shape
     Co = w.shape[0]
     L = lib()
-    ws = _ws(L.shl_nn_conv3x3_workspace_floats(B, Ci, Co, H, W), x)
     gw = torch.empty_like(w)
     gb = torch.empty(Co, dtype=torch.float32, device=x.device)
-    _chk("conv3x3_backward_weight", L.shl_nn_conv3x3_backward_weight(
-        _p(x), _p(gout), _p(gw), _p(gb), B, Ci, Co, H, W, _p(ws), _st(x)))
+    if tc_w:
+        shl_nn_conv3x3_backward_weight_tc(x, gout, gw, gb)
+    ws = _ws(L.shl_nn_conv3x3_workspace_floats(B, Ci, Co, H, W), x) if (not tc_w or
+                                                                      (need_gin and not tc)) else None
+    if not tc_w:
+        _chk("conv3x3_backward_weight", L.shl_nn_conv3x3_backward_weight(
+            _p(x), _p(gout), _p(gw), _p(gb), B, Ci, Co, H, W, _p(ws), _st(x)))
     gin = None
     if need_gin:
         gin = torch.empty_like(x)
@@ -157,6 +177,7 @@ class _Conv3x3(torch.autograd.Function):
         # tensor cores for the forward and the input gradient where the shape allows
         ctx.tc_fwd = bool(tc) and shl_nn_conv3x3_tc_supported(Ci, Co, H, W)
         ctx.tc_bwd = bool(tc) and shl_nn_conv3x3_tc_supported(Co, Ci, H, W)
+        ctx.tc_w = bool(tc) and shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)
         if ctx.tc_fwd:
             shl_nn_conv3x3_forward_tc(x, w.contiguous(), b.contiguous(), out)
         else:
@@ -168,7 +189,8 @@ class _Conv3x3(torch.autograd.Function):
     def backward(ctx, gout):
         x, w = ctx.saved_tensors
         gin, gw, gb = shl_nn_conv3x3_backward(x, w.contiguous(), gout.contiguous(),
-                                             ctx.needs_input_grad[0], tc=ctx.tc_bwd)
+                                             ctx.needs_input_grad[0], tc=ctx.tc_bwd,
+                                             tc_w=ctx.tc_w)
         return gin, gw, gb, None
 
 
@@ -320,9 +342,9 @@ class _MSE(torch.autograd.Function):
 
 
 def conv3x3(x, w, b, tc=False):
-    """3x3 convolution; tc=True runs the forward and the input gradient on
-    the tensor cores (bfloat16 operands, float32 accumulation) when
-    shl_nn_conv3x3_tc_supported, else the float32 kernels."""
+    """3x3 convolution; tc=True runs the forward, the input gradient and the
+    weight gradient on the tensor cores (bfloat16 operands, float32
+    accumulation) where the shapes are supported, else the float32 kernels."""
     return _Conv3x3.apply(x, w, b, tc)
 
 

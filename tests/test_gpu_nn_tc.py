@@ -59,11 +59,32 @@ def test_tc_backward_data_matches_rounded_oracle(B, Ci, Co, H, W):
     assert _rel(gin, xo.grad) <= TOL
 
 
+WSHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 42, 48, 2, 128),
+           (3, 32, 16, 1, 128), (1, 7, 5, 6, 256)]
+
+
+@pytest.mark.parametrize("B,Ci,Co,H,W", WSHAPES)
+def test_tc_weight_gradient_matches_rounded_oracle(B, Ci, Co, H, W):
+    from paper_2006_04591_gb300 import nn
+    assert nn.shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)
+    gen = torch.Generator().manual_seed(B * 31 + Ci * 7 + Co)
+    x = torch.randn((B, Ci, H, W), generator=gen)
+    gout = torch.randn((B, Co, H, W), generator=gen)
+    gw = torch.empty((Co, Ci, 3, 3), device="cuda")
+    gb = torch.empty(Co, device="cuda")
+    nn.shl_nn_conv3x3_backward_weight_tc(x.cuda(), gout.cuda(), gw, gb)
+    nn.shl_nn_tc_status()
+    want = torch.nn.grad.conv2d_weight(_bf(x), (Co, Ci, 3, 3), _bf(gout), padding=1)
+    assert _rel(gw, want) <= 1e-4
+    assert _rel(gb, gout.double().sum((0, 2, 3))) <= 1e-5
+
+
 def test_tc_rejects_unsupported_shapes():
     from paper_2006_04591_gb300 import nn
     from paper_2006_04591_gb300.shearlet import ShearletError
     assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 100)
     assert not nn.shl_nn_conv3x3_tc_supported(64, 32, 8, 128)
+    assert not nn.shl_nn_conv3x3_wgrad_tc_supported(43, 32, 8, 128)
     x = torch.zeros((1, 32, 8, 100), device="cuda")
     with pytest.raises(ShearletError):
         nn.shl_nn_conv3x3_forward_tc(x, torch.zeros((32, 32, 3, 3), device="cuda"), None,
@@ -72,8 +93,8 @@ def test_tc_rejects_unsupported_shapes():
 
 class _RoundedConv(torch.autograd.Function):
     """float64 reference of what the tensor-core path computes: the forward
-    and the input gradient see bfloat16-rounded operands, the weight gradient
-    (float32 kernel on the GPU) the unrounded ones."""
+    and both gradients see bfloat16-rounded operands (the bias gradient the
+    unrounded output gradient)."""
 
     @staticmethod
     def forward(ctx, x, w, b):
@@ -85,7 +106,7 @@ class _RoundedConv(torch.autograd.Function):
         x, w = ctx.saved_tensors
         F = torch.nn.grad
         gin = F.conv2d_input(x.shape, _bf(w), _bf(g), padding=1)
-        gw = F.conv2d_weight(x, w.shape, g, padding=1)
+        gw = F.conv2d_weight(_bf(x), w.shape, _bf(g), padding=1)
         return gin, gw, g.sum((0, 2, 3))
 
 
