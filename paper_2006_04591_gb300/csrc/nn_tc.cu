@@ -4,9 +4,9 @@
 // Implicit GEMM per tile of 128 consecutive output pixels of one image row:
 //   D[m][n] = sum_{tap, ci} P_tap[m][ci] * W_tap[n][ci]
 // with P_tap[m][ci] = in[ci][y + dy - 1][x0 + m + dx - 1] (zero padding).
-// The CTA stages the three input rows it needs once, as bfloat16, in the
-// no-swizzle K-major core-matrix layout [row][ci/8][pixel][8 ci] (16 bytes
-// per pixel and channel group), loading float4 groups of 4 pixels.  Consecutive pixels are 16 bytes apart, so
+// The CTA stages input rows as bfloat16 in the no-swizzle K-major
+// core-matrix layout [ci/8][pixel][8 ci] (16 bytes per pixel and channel
+// group), loading float4 groups of 4 pixels, into a ring of four rows.  Consecutive pixels are 16 bytes apart, so
 // the A operand of tap (dy, dx) is the same staged rows with its start
 // address moved by dx * 16 bytes: no im2col copy.  The weights sit in the
 // same layout [tap][ci/8][n][8 ci] for the whole launch.  One thread issues
@@ -44,6 +44,7 @@ struct ConvTcArgs {
   float* out;           // [B][Cout][H][W]
   int B, Cin, Cout, H, W;
   int flip;             // 1: convolution with the flipped, channel-transposed weights
+  int rows_per_unit;    // output rows one CTA walks down per unit
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -114,18 +115,57 @@ template <int CG, int NP>
 struct ConvTcT {
   static_assert(CG % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 64, "tile shape");
   static constexpr int KS = CG / 2;                          // K steps of 16 per tap
+  static constexpr int SLOTS = 4;                            // input-row ring
   static constexpr size_t WBYTES = (size_t)9 * CG * NP * 16;  // [tap][cg][n][8]
-  static constexpr size_t PBYTES = (size_t)3 * CG * PW * 16;  // [row][cg][px][8]
-  static constexpr size_t SMEM = WBYTES + PBYTES;            // descriptors stay inside
+  static constexpr size_t RBYTES = (size_t)CG * PW * 16;      // one row: [cg][px][8]
+  static constexpr size_t SMEM = WBYTES + SLOTS * RBYTES;    // descriptors stay inside
   static constexpr uint32_t NCOLS = NP <= 32 ? 32 : 64;       // TMEM columns (power of 2)
 };
 
+// Stage input row gy of image b (zeros outside the image), pixels
+// x0-4..x0+131, as bfloat16 [cg][px][8] into `dst`: one item = 4 pixels x 8
+// channels (8 float4 loads, 4 16-byte stores).
+template <int CG>
+__device__ __forceinline__ void stage_row(const ConvTcArgs& a, uint8_t* dst, int b, int gy, int x0,
+                                          int tid) {
+  constexpr int PG = PW / 4;
+  const size_t cs = (size_t)a.H * a.W;
+  const bool rok = gy >= 0 && gy < a.H;
+  for (int idx = tid; idx < CG * PG; idx += TC_THREADS) {
+    const int cg = idx / PG, q = idx - cg * PG;
+    const int gx = x0 - 4 + 4 * q;
+    const bool ok = rok && gx >= 0 && gx < a.W;
+    const float* src = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W + (ok ? gx : 0);
+    float4 v[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+      v[c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    uint8_t* d = dst + ((size_t)cg * PW + 4 * q) * 16;
+    *reinterpret_cast<uint4*>(d) = make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x),
+                                              pack_bf16(v[4].x, v[5].x), pack_bf16(v[6].x, v[7].x));
+    *reinterpret_cast<uint4*>(d + 16) =
+        make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y), pack_bf16(v[4].y, v[5].y),
+                   pack_bf16(v[6].y, v[7].y));
+    *reinterpret_cast<uint4*>(d + 32) =
+        make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z), pack_bf16(v[4].z, v[5].z),
+                   pack_bf16(v[6].z, v[7].z));
+    *reinterpret_cast<uint4*>(d + 48) =
+        make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w), pack_bf16(v[4].w, v[5].w),
+                   pack_bf16(v[6].w, v[7].w));
+  }
+}
+
+// A CTA takes units of (image, 128-pixel column, run of a.rows_per_unit
+// rows) and walks down the rows with a ring of four staged input rows: row
+// y + 2 is staged while the MMAs of row y run, so each output row costs one
+// new input row.
 template <int CG, int NP>
 __global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
   using P = ConvTcT<CG, NP>;
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* wsm = sm;
-  uint8_t* patch = sm + P::WBYTES;
+  uint8_t* ring = sm + P::WBYTES;
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
@@ -157,95 +197,76 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     s_fail = 0;
   }
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // weights -> async proxy
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_bf16(TC_M, NP);
-  const uint32_t wbase = smem_u32(wsm), pbase = smem_u32(patch);
+  const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(ring);
+  const size_t cs = (size_t)a.H * a.W;
 
   const int tiles_x = a.W / TC_M;
-  const int ntiles = a.B * a.H * tiles_x;
+  const int RU = a.rows_per_unit;
+  const int runs = (a.H + RU - 1) / RU;
+  const int nunits = a.B * tiles_x * runs;
   uint32_t phase = 0;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int b = tile / (a.H * tiles_x), rem = tile - b * a.H * tiles_x;
-    const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * TC_M;
-    // input rows y-1..y+1, pixels x0-4..x0+131 -> bfloat16 [row][cg][px][8],
-    // one item = 4 pixels x 8 channels (8 float4 loads, 4 16-byte stores)
-    constexpr int PG = PW / 4;
-    const size_t cs = (size_t)a.H * a.W;
-    for (int idx = tid; idx < 3 * CG * PG; idx += TC_THREADS) {
-      const int r = idx / (CG * PG), rem2 = idx - r * CG * PG, cg = rem2 / PG, q = rem2 - cg * PG;
-      const int gy = y - 1 + r, gx = x0 - 4 + 4 * q;
-      const bool ok = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
-      const float* src = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W + (ok ? gx : 0);
-      float4 v[8];
+  for (int u = blockIdx.x; u < nunits && !s_fail; u += gridDim.x) {
+    const int b = u / (tiles_x * runs), rem = u - b * tiles_x * runs;
+    const int xt = rem / runs, y0 = (rem - xt * runs) * RU, y1 = min(a.H, y0 + RU);
+    const int x0 = xt * TC_M;
+    // the three rows of the first output row; the previous unit's MMAs are done
+    for (int gy = y0 - 1; gy <= y0 + 1; ++gy)
+      stage_row<CG>(a, ring + (size_t)((gy + 4) & 3) * P::RBYTES, b, gy, x0, tid);
+    for (int y = y0; y < y1; ++y) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged rows -> async proxy
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < 8; ++c)
-        v[c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
-                                          : make_float4(0.f, 0.f, 0.f, 0.f);
-      uint8_t* dst = patch + ((size_t)(r * CG + cg) * PW + 4 * q) * 16;
-      *reinterpret_cast<uint4*>(dst) =
-          make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x),
-                     pack_bf16(v[4].x, v[5].x), pack_bf16(v[6].x, v[7].x));
-      *reinterpret_cast<uint4*>(dst + 16) =
-          make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y),
-                     pack_bf16(v[4].y, v[5].y), pack_bf16(v[6].y, v[7].y));
-      *reinterpret_cast<uint4*>(dst + 32) =
-          make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z),
-                     pack_bf16(v[4].z, v[5].z), pack_bf16(v[6].z, v[7].z));
-      *reinterpret_cast<uint4*>(dst + 48) =
-          make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w),
-                     pack_bf16(v[4].w, v[5].w), pack_bf16(v[6].w, v[7].w));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // patch -> async proxy
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
+        for (int t = 0; t < 9; ++t) {
+          const int dy = t / 3, dx = t - dy * 3;
+          const uint32_t row = rbase + (uint32_t)(((y + dy - 1 + 4) & 3) * P::RBYTES);
 #pragma unroll
-      for (int t = 0; t < 9; ++t) {
-        const int dy = t / 3, dx = t - dy * 3;
-#pragma unroll
-        for (int s = 0; s < P::KS; ++s) {
-          const uint64_t ad = mdesc(pbase + (uint32_t)(((dy * CG + 2 * s) * PW + dx + PX0) * 16),
-                                    PW * 16, 128);
-          const uint64_t bd = mdesc(wbase + (uint32_t)(((t * CG + 2 * s) * NP) * 16), NP * 16, 128);
-          const uint32_t acc = (t | s) != 0;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+          for (int s = 0; s < P::KS; ++s) {
+            const uint64_t ad = mdesc(row + (uint32_t)(((2 * s) * PW + dx + PX0) * 16), PW * 16, 128);
+            const uint64_t bd = mdesc(wbase + (uint32_t)(((t * CG + 2 * s) * NP) * 16), NP * 16, 128);
+            const uint32_t acc = (t | s) != 0;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
         }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar))
+            : "memory");
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar))
-          : "memory");
+      // row y + 2 goes to the slot of row y - 2, which no MMA in flight reads
+      if (y + 1 < y1) stage_row<CG>(a, ring + (size_t)((y + 2) & 3) * P::RBYTES, b, y + 2, x0, tid);
+      if (!mbar_wait(smem_u32(&mbar), phase)) {
+        atomicOr(&g_tc_err, 1u);
+        s_fail = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      if (s_fail) break;
+      tc_fence_after();
+      uint32_t acc[NP];
+#pragma unroll
+      for (int q = 0; q < NP / 16; ++q)
+        SHL_TMEM_LD16(acc + 16 * q, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x0 + warp * 32 + lane;
+#pragma unroll
+      for (int n = 0; n < NP; ++n) {
+        if (n < a.Cout) o[n * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + n) : 0.f);
+      }
+      tc_fence_before();   // TMEM reads done before the next row's MMAs (barrier at loop top)
     }
-    if (!mbar_wait(smem_u32(&mbar), phase)) {
-      atomicOr(&g_tc_err, 1u);
-      s_fail = 1;
-    }
-    phase ^= 1u;
     __syncthreads();
-    if (s_fail) break;
-    tc_fence_after();
-    uint32_t acc[NP];
-#pragma unroll
-    for (int q = 0; q < NP / 16; ++q)
-      SHL_TMEM_LD16(acc + 16 * q, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-    const int x = x0 + warp * 32 + lane;
-    float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x;
-#pragma unroll
-    for (int n = 0; n < NP; ++n) {
-      if (n < a.Cout) o[n * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + n) : 0.f);
-    }
-    tc_fence_before();
-    __syncthreads();   // TMEM accumulator and patch free for the next tile
   }
   tc_fence_before();
   __syncthreads();
@@ -268,7 +289,7 @@ __global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
 struct WgradTcArgs {
   const float* in;      // [B][Cin][H][W]
   const float* gout;    // [B][Cout][H][W]
-  float* part;          // [gridDim.x][Cout][Cin][9]
+  float* part;          // [gridDim.x][Cout * Cin * 9 + Cout]: weight then bias partials
   int B, Cin, Cout, H, W;
 };
 
@@ -279,6 +300,7 @@ struct WgradTcT {
   static constexpr size_t BBYTES = (size_t)PG * NP * 16;    // [pg][o][8]
   static constexpr size_t SMEM = 3 * ABYTES + BBYTES;
   static constexpr uint32_t NCOLS = 3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : 256);
+  static constexpr int BITEMS = (NP * PG + TC_THREADS - 1) / TC_THREADS;   // gout items per thread
 };
 
 template <int NP>
@@ -317,18 +339,27 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
   const int nunits = a.B * a.H * tiles_x;
   uint32_t phase = 0;
   bool first = true;
+  float bsum[P::BITEMS];   // bias partials of this thread's fixed gout items, float32
+#pragma unroll
+  for (int k = 0; k < P::BITEMS; ++k) bsum[k] = 0.f;
   for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
     const int b = u / (a.H * tiles_x), rem = u - b * a.H * tiles_x;
     const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * TC_M;
-    // B: gout rows, 8 pixels per item
-    for (int idx = tid; idx < a.Cout * P::PG; idx += TC_THREADS) {
-      const int o = idx / P::PG, pg = idx - o * P::PG;
-      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
-      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-      *reinterpret_cast<uint4*>(Bs + ((size_t)pg * NP + o) * 16) =
-          make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
-                     pack_bf16(v1.z, v1.w));
+    // B: gout rows, 8 pixels per item (item idx = o * PG + pg, the same for
+    // every unit, so each thread's bias partial covers fixed channels)
+#pragma unroll
+    for (int k = 0; k < P::BITEMS; ++k) {
+      const int idx = tid + k * TC_THREADS;
+      if (idx < a.Cout * P::PG) {
+        const int o = idx / P::PG, pg = idx - o * P::PG;
+        const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+        bsum[k] += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
+        *reinterpret_cast<uint4*>(Bs + ((size_t)pg * NP + o) * 16) =
+            make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
+                       pack_bf16(v1.z, v1.w));
+      }
     }
     // A: for each dy and input channel, 10 input pixels give the three
     // shifted 8-pixel rows (dx = 0, 1, 2)
@@ -392,12 +423,26 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
     __syncthreads();
     if (s_fail) break;
   }
+  // bias partial of this CTA: item partials through shared memory (the
+  // staging area is free now), summed per channel in pixel-group order
+  float* bred = reinterpret_cast<float*>(sm);
+#pragma unroll
+  for (int k = 0; k < P::BITEMS; ++k) {
+    const int idx = tid + k * TC_THREADS;
+    if (idx < a.Cout * P::PG) bred[idx] = bsum[k];
+  }
+  __syncthreads();
+  if (tid < a.Cout) {
+    float s = 0.f;
+    for (int pg = 0; pg < P::PG; ++pg) s += bred[tid * P::PG + pg];
+    a.part[(size_t)blockIdx.x * (a.Cout * a.Cin * 9 + a.Cout) + a.Cout * a.Cin * 9 + tid] = s;
+  }
   // epilogue: lane r = dx * Cin + i of warp r / 32, columns dy * NP + o
   if (!s_fail) {
     tc_fence_after();
     const int r = warp * 32 + lane;
     const int dx = r / a.Cin, i = r - dx * a.Cin;
-    float* part = a.part + (size_t)blockIdx.x * a.Cout * a.Cin * 9;
+    float* part = a.part + (size_t)blockIdx.x * (a.Cout * a.Cin * 9 + a.Cout);
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
       uint32_t acc[NP];
@@ -424,34 +469,17 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
                  : "memory");
 }
 
-// gw[e] = sum_c part[c][e] in CTA order; gb[o] = sum over b, pixels of gout
-// (one CTA per channel, fixed thread mapping, tree reduction).
-__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ gw, int nparts,
-                               int n) {
+// Sum the per-CTA partials in CTA order: entries e < nw are the weight
+// gradient, the next Cout the bias gradient (written only if gb != null).
+__global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict__ gw,
+                               float* __restrict__ gb, int nparts, int nw, int nb) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int n = nw + nb;
   if (e >= n) return;
   float s = 0.f;
   for (int c = 0; c < nparts; ++c) s += part[(size_t)c * n + e];
-  gw[e] = s;
-}
-
-__global__ void __launch_bounds__(256) k_bias_grad(const float* __restrict__ gout,
-                                                   float* __restrict__ gb, int B, int C,
-                                                   long long HW) {
-  const int o = blockIdx.x;
-  float s = 0.f;
-  for (int b = 0; b < B; ++b) {
-    const float* p = gout + ((size_t)b * C + o) * HW;
-    for (long long q = threadIdx.x; q < HW; q += blockDim.x) s += p[q];
-  }
-  __shared__ float red[256];
-  red[threadIdx.x] = s;
-  __syncthreads();
-  for (int w = 128; w > 0; w >>= 1) {
-    if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) gb[o] = red[0];
+  if (e < nw) gw[e] = s;
+  else if (gb) gb[e - nw] = s;
 }
 
 int wgrad_grid(int B, int H, int W) {
@@ -481,16 +509,25 @@ cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   auto k = k_conv3x3_tc<CG, NP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
   if (e) return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC_THREADS, P::SMEM))) return e;
-  // TMEM: at most 512 columns per SM between the resident CTAs
-  per_sm = std::max(1, std::min(per_sm, (int)(512 / P::NCOLS)));
+  // CTAs per SM for the grid size: the shared-memory bound (228 KB per SM,
+  // 1 KB reserved per CTA), at most 8 and at most 512 TMEM columns.  No CTA
+  // waits on another, so the count only sizes the grid.
+  int per_sm = (int)((228u * 1024u) / (P::SMEM + 1024u + 256u));
+  per_sm = std::max(1, std::min({per_sm, 8, (int)(512 / P::NCOLS)}));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int ntiles = a.B * a.H * (a.W / TC_M);
-  const int grid = std::max(1, std::min(ntiles, per_sm * std::max(sms, 1)));
-  k<<<grid, TC_THREADS, P::SMEM, st>>>(a);
+  const int slots = per_sm * std::max(sms, 1);
+  // rows per unit: about four units per CTA, 4..32 rows (two extra input
+  // rows are staged per unit)
+  const long long strips = (long long)a.B * (a.W / TC_M);
+  const long long rows = strips * a.H;
+  ConvTcArgs args = a;
+  args.rows_per_unit = (int)std::max(4LL, std::min(32LL, rows / std::max(1LL, 4LL * slots)));
+  args.rows_per_unit = std::min(args.rows_per_unit, a.H);
+  const long long nunits = strips * ((a.H + args.rows_per_unit - 1) / args.rows_per_unit);
+  const int grid = (int)std::max(1LL, std::min(nunits, (long long)slots));
+  k<<<grid, TC_THREADS, P::SMEM, st>>>(args);
   return cudaGetLastError();
 }
 
@@ -535,7 +572,7 @@ shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const floa
     g_tc_msg = "conv3x3_forward_tc: bad arguments, unsupported shape or input not 16-byte aligned";
     return SHL_EINVAL;
   }
-  const ConvTcArgs a{in, w, bias, out, B, Ci, Co, H, W, 0};
+  const ConvTcArgs a{in, w, bias, out, B, Ci, Co, H, W, 0, 1};
   return tc_run(a, stream, "conv3x3_forward_tc: launch failed");
 }
 
@@ -547,7 +584,7 @@ shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, fl
     return SHL_EINVAL;
   }
   // gin = conv(gout, flipped and channel-transposed w): Cin = Co, Cout = Ci
-  const ConvTcArgs a{gout, w, nullptr, gin, B, Co, Ci, H, W, 1};
+  const ConvTcArgs a{gout, w, nullptr, gin, B, Co, Ci, H, W, 1, 1};
   return tc_run(a, stream, "conv3x3_backward_data_tc: launch failed");
 }
 
@@ -557,7 +594,7 @@ int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W) {
 
 size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W) {
   if (B < 1 || !shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)) return 0;
-  return (size_t)wgrad_grid(B, H, W) * Co * Ci * 9;
+  return (size_t)wgrad_grid(B, H, W) * ((size_t)Co * Ci * 9 + Co);
 }
 
 shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout, float* gw,
@@ -576,9 +613,8 @@ shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout,
                 : np == 32 ? launch_wgrad<32>(a, grid, st)
                            : launch_wgrad<48>(a, grid, st);
   if (e == cudaSuccess) {
-    const int n = Co * Ci * 9;
-    k_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(ws, gw, grid, n);
-    if (gb) k_bias_grad<<<Co, 256, 0, st>>>(gout, gb, B, Co, (long long)H * W);
+    const int nw = Co * Ci * 9;
+    k_wgrad_reduce<<<(nw + Co + 255) / 256, 256, 0, st>>>(ws, gw, gb, grid, nw, Co);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
