@@ -34,6 +34,7 @@ shl_status nn_launch(const char* where) {
   return SHL_OK;
 }
 inline cudaStream_t S(void* s) { return static_cast<cudaStream_t>(s); }
+inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 inline int blocks(long long n, int t) { return (int)std::min<long long>((n + t - 1) / t, 1 << 20); }
 
 // ------------------------------------------------------------ conv 3x3
@@ -205,10 +206,19 @@ __global__ void k_conv_wgrad_reduce(const float* __restrict__ partial, float* __
 
 // ------------------------------------------------------------ elementwise
 __global__ void k_prelu_fwd(const float* __restrict__ x, const float* __restrict__ a,
-                            float* __restrict__ y, long long n) {
+                            float* __restrict__ y, long long n, int vec) {
   const float s = a[0];
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long n4 = vec ? n / 4 : 0;               // float4 body (16-byte aligned pointers)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+    float4 v = __ldcs(reinterpret_cast<const float4*>(x) + i);
+    v.x = v.x >= 0.f ? v.x : s * v.x;
+    v.y = v.y >= 0.f ? v.y : s * v.y;
+    v.z = v.z >= 0.f ? v.z : s * v.z;
+    v.w = v.w >= 0.f ? v.w : s * v.w;
+    reinterpret_cast<float4*>(y)[i] = v;
+  }
+  for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
     const float v = x[i];
     y[i] = v >= 0.f ? v : s * v;
   }
@@ -219,11 +229,27 @@ __global__ void __launch_bounds__(256) k_prelu_bwd(const float* __restrict__ x,
                                                    const float* __restrict__ a,
                                                    const float* __restrict__ gy,
                                                    float* __restrict__ gx,
-                                                   float* __restrict__ partial, long long n) {
+                                                   float* __restrict__ partial, long long n,
+                                                   int vec) {
   const float s = a[0];
   float acc = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
+  const long long n4 = vec ? n / 4 : 0;               // float4 body (16-byte aligned pointers)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += stride) {
+    const float4 v = __ldcs(reinterpret_cast<const float4*>(x) + i);
+    const float4 g = __ldcs(reinterpret_cast<const float4*>(gy) + i);
+    float4 o;
+    o.x = v.x >= 0.f ? g.x : s * g.x;
+    o.y = v.y >= 0.f ? g.y : s * g.y;
+    o.z = v.z >= 0.f ? g.z : s * g.z;
+    o.w = v.w >= 0.f ? g.w : s * g.w;
+    reinterpret_cast<float4*>(gx)[i] = o;
+    if (v.x < 0.f) acc = fmaf(g.x, v.x, acc);
+    if (v.y < 0.f) acc = fmaf(g.y, v.y, acc);
+    if (v.z < 0.f) acc = fmaf(g.z, v.z, acc);
+    if (v.w < 0.f) acc = fmaf(g.w, v.w, acc);
+  }
+  for (long long i = 4 * n4 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
     const float v = x[i], g = gy[i];
     gx[i] = v >= 0.f ? g : s * g;
     if (v < 0.f) acc = fmaf(g, v, acc);
@@ -467,9 +493,18 @@ __global__ void k_mask_mix_bwd(const uint8_t* __restrict__ mask, const float* __
 }
 
 __global__ void k_bf16_to_f32(const __nv_bfloat16* __restrict__ x, float* __restrict__ y,
-                              long long n) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
+                              long long n, int vec) {
+  const long long n8 = vec ? n / 8 : 0;               // 16-byte body (16-byte aligned pointers)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n8; i += stride) {
+    const uint4 h = __ldcs(reinterpret_cast<const uint4*>(x) + i);
+    const __nv_bfloat162* p = reinterpret_cast<const __nv_bfloat162*>(&h);
+    const float2 a = __bfloat1622float2(p[0]), b = __bfloat1622float2(p[1]);
+    const float2 c = __bfloat1622float2(p[2]), d = __bfloat1622float2(p[3]);
+    reinterpret_cast<float4*>(y)[2 * i] = make_float4(a.x, a.y, b.x, b.y);
+    reinterpret_cast<float4*>(y)[2 * i + 1] = make_float4(c.x, c.y, d.x, d.y);
+  }
+  for (long long i = 8 * n8 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
     y[i] = __bfloat162float(x[i]);
 }
 __global__ void k_f32_to_bf16(const float* __restrict__ x, __nv_bfloat16* __restrict__ y,
@@ -550,7 +585,8 @@ shl_status shl_nn_conv3x3_backward_weight(const float* in, const float* gout, fl
 shl_status shl_nn_prelu_forward(const float* x, const float* a, float* y, long long n, void* stream) {
   if (!x || !a || !y || n < 0) return nn_fail(SHL_EINVAL, "prelu_forward: bad arguments");
   if (n == 0) return SHL_OK;
-  k_prelu_fwd<<<blocks(n, 256), 256, 0, S(stream)>>>(x, a, y, n);
+  const int vec = aligned16(x) && aligned16(y);
+  k_prelu_fwd<<<blocks(vec ? (n + 3) / 4 : n, 256), 256, 0, S(stream)>>>(x, a, y, n, vec);
   return nn_launch("prelu_forward");
 }
 
@@ -563,7 +599,8 @@ shl_status shl_nn_prelu_backward(const float* x, const float* a, const float* gy
                                  float* ga, long long n, float* ws, void* stream) {
   if (!x || !a || !gy || !gx || !ga || !ws || n < 0) return nn_fail(SHL_EINVAL, "prelu_backward: bad arguments");
   const int g = std::max(1, std::min(RED_CTAS, blocks(n, 256)));
-  k_prelu_bwd<<<g, 256, 0, S(stream)>>>(x, a, gy, gx, ws, n);
+  const int vec = aligned16(x) && aligned16(gy) && aligned16(gx);
+  k_prelu_bwd<<<g, 256, 0, S(stream)>>>(x, a, gy, gx, ws, n, vec);
   k_sum<<<1, 256, 0, S(stream)>>>(ws, g, ga);
   return nn_launch("prelu_backward");
 }
@@ -694,10 +731,11 @@ shl_status shl_nn_mask_mix_backward(const unsigned char* mask, const float* gu, 
 shl_status shl_nn_cast(const void* x, int x_bf16, void* y, long long n, void* stream) {
   if (!x || !y) return nn_fail(SHL_EINVAL, "cast: bad arguments");
   if (n == 0) return SHL_OK;
-  if (x_bf16)
-    k_bf16_to_f32<<<blocks(n, 256), 256, 0, S(stream)>>>(static_cast<const __nv_bfloat16*>(x),
-                                                         static_cast<float*>(y), n);
-  else
+  if (x_bf16) {
+    const int vec = aligned16(x) && aligned16(y);
+    k_bf16_to_f32<<<blocks(vec ? (n + 7) / 8 : n, 256), 256, 0, S(stream)>>>(
+        static_cast<const __nv_bfloat16*>(x), static_cast<float*>(y), n, vec);
+  } else
     k_f32_to_bf16<<<blocks(n, 256), 256, 0, S(stream)>>>(static_cast<const float*>(x),
                                                          static_cast<__nv_bfloat16*>(y), n);
   return nn_launch("cast");

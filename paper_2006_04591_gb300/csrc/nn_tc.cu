@@ -161,7 +161,7 @@ __device__ __forceinline__ void stage_row(const ConvTcArgs& a, uint8_t* dst, int
 // y + 2 is staged while the MMAs of row y run, so each output row costs one
 // new input row.
 template <int CG, int NP>
-__global__ void __launch_bounds__(TC_THREADS) k_conv3x3_tc(ConvTcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
   using P = ConvTcT<CG, NP>;
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* wsm = sm;
@@ -291,31 +291,94 @@ struct WgradTcArgs {
   const float* gout;    // [B][Cout][H][W]
   float* part;          // [gridDim.x][Cout * Cin * 9 + Cout]: weight then bias partials
   int B, Cin, Cout, H, W;
+  int rows_per_unit;    // output rows one CTA walks down per unit
 };
 
 template <int NP>
 struct WgradTcT {
-  static constexpr int PG = TC_M / 8;                       // pixel groups per unit
-  static constexpr size_t ABYTES = (size_t)PG * 128 * 16;   // one dy: [pg][r][8]
-  static constexpr size_t BBYTES = (size_t)PG * NP * 16;    // [pg][o][8]
-  static constexpr size_t SMEM = 3 * ABYTES + BBYTES;
+  static constexpr int THREADS = 256;                       // 8 warps stage, 4 read TMEM
+  static constexpr int PG = TC_M / 8;                       // pixel groups per unit row
+  static constexpr int SLOTS = 4;                           // input-row ring
+  static constexpr size_t ABYTES = (size_t)PG * 128 * 16;   // one input row: [pg][r][8]
+  static constexpr size_t BBYTES = (size_t)PG * NP * 16;    // one gout row: [pg][o][8]
+  static constexpr size_t SMEM = SLOTS * ABYTES + 2 * BBYTES;
   static constexpr uint32_t NCOLS = 3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : 256);
-  static constexpr int BITEMS = (NP * PG + TC_THREADS - 1) / TC_THREADS;   // gout items per thread
+  static constexpr int BITEMS = (NP * PG + THREADS - 1) / THREADS;   // gout items per thread
 };
 
+// Input row gy (zeros outside the image) -> the three shifted copies
+// A[r = dx * Cin + i][p] = in[i][gy][x0 + p + dx - 1], bfloat16 [pg][r][8].
 template <int NP>
-__global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
+__device__ __forceinline__ void wgrad_stage_in(const WgradTcArgs& a, uint8_t* dst, int b, int gy,
+                                               int x0, int tid) {
+  using P = WgradTcT<NP>;
+  const bool rok = gy >= 0 && gy < a.H;
+  for (int idx = tid; idx < a.Cin * P::PG; idx += P::THREADS) {
+    const int i = idx / P::PG, pg = idx - i * P::PG;
+    const int xs = x0 + 8 * pg;
+    float e[10];
+    if (rok) {
+      const float* src = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W + xs;
+      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
+      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+      e[0] = xs > 0 ? __ldg(src - 1) : 0.f;
+      e[1] = v0.x; e[2] = v0.y; e[3] = v0.z; e[4] = v0.w;
+      e[5] = v1.x; e[6] = v1.y; e[7] = v1.z; e[8] = v1.w;
+      e[9] = xs + 8 < a.W ? __ldg(src + 8) : 0.f;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 10; ++c) e[c] = 0.f;
+    }
+    uint8_t* d = dst + ((size_t)pg * 128 + i) * 16;
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx)   // pixel x0+8pg+j-1+dx = e[j + dx]
+      *reinterpret_cast<uint4*>(d + (size_t)dx * a.Cin * 16) =
+          make_uint4(pack_bf16(e[dx], e[dx + 1]), pack_bf16(e[dx + 2], e[dx + 3]),
+                     pack_bf16(e[dx + 4], e[dx + 5]), pack_bf16(e[dx + 6], e[dx + 7]));
+  }
+}
+
+// gout row y -> a B buffer, bfloat16 [pg][o][8], 8 pixels per item (item
+// o * PG + pg, the same for every row, so bsum[k] is this thread's float32
+// bias partial of fixed channels).
+template <int NP>
+__device__ __forceinline__ void wgrad_stage_gout(const WgradTcArgs& a, uint8_t* dst, int b, int y,
+                                                 int x0, int tid,
+                                                 float (&bsum)[WgradTcT<NP>::BITEMS]) {
+  using P = WgradTcT<NP>;
+#pragma unroll
+  for (int k = 0; k < P::BITEMS; ++k) {
+    const int idx = tid + k * P::THREADS;
+    if (idx < a.Cout * P::PG) {
+      const int o = idx / P::PG, pg = idx - o * P::PG;
+      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
+      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
+      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+      bsum[k] += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
+      *reinterpret_cast<uint4*>(dst + ((size_t)pg * NP + o) * 16) =
+          make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
+                     pack_bf16(v1.z, v1.w));
+    }
+  }
+}
+
+// A CTA takes units of (image, 128-pixel column, run of a.rows_per_unit
+// output rows) and walks down the rows: input rows in a ring of four slots
+// (row y + 2 staged while the MMAs of row y run), gout rows double-buffered;
+// every MMA of the launch accumulates into the same three TMEM tiles.
+template <int NP>
+__global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcArgs a) {
   using P = WgradTcT<NP>;
   extern __shared__ __align__(128) uint8_t sm[];
-  uint8_t* As = sm;                       // 3 x [pg][128][8]
-  uint8_t* Bs = sm + 3 * P::ABYTES;       // [pg][NP][8]
+  uint8_t* As = sm;                           // SLOTS x [pg][128][8]
+  uint8_t* Bs = sm + P::SLOTS * P::ABYTES;    // 2 x [pg][NP][8]
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tmem_slot;
   __shared__ int s_fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // rows r >= 3 Cin and o >= Cout stay zero for the whole launch
-  for (size_t q = tid; q < P::SMEM / 16; q += TC_THREADS)
+  for (size_t q = tid; q < P::SMEM / 16; q += P::THREADS)
     reinterpret_cast<uint4*>(sm)[q] = make_uint4(0u, 0u, 0u, 0u);
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -336,113 +399,90 @@ __global__ void __launch_bounds__(TC_THREADS) k_wgrad_tc(WgradTcArgs a) {
   const uint32_t idesc = idesc_bf16(TC_M, NP);
   const uint32_t abase = smem_u32(As), bbase = smem_u32(Bs);
   const int tiles_x = a.W / TC_M;
-  const int nunits = a.B * a.H * tiles_x;
+  const int RU = a.rows_per_unit;
+  const int runs = (a.H + RU - 1) / RU;
+  const int nunits = a.B * tiles_x * runs;
   uint32_t phase = 0;
   bool first = true;
   float bsum[P::BITEMS];   // bias partials of this thread's fixed gout items, float32
 #pragma unroll
   for (int k = 0; k < P::BITEMS; ++k) bsum[k] = 0.f;
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const int b = u / (a.H * tiles_x), rem = u - b * a.H * tiles_x;
-    const int y = rem / tiles_x, x0 = (rem - y * tiles_x) * TC_M;
-    // B: gout rows, 8 pixels per item (item idx = o * PG + pg, the same for
-    // every unit, so each thread's bias partial covers fixed channels)
+
+  for (int u = blockIdx.x; u < nunits && !s_fail; u += gridDim.x) {
+    const int b = u / (tiles_x * runs), rem = u - b * tiles_x * runs;
+    const int xt = rem / runs, y0 = (rem - xt * runs) * RU, y1 = min(a.H, y0 + RU);
+    const int x0 = xt * TC_M;
+    // the previous unit's MMAs are done: stage rows y0-1..y0+1 and gout row y0
+    for (int gy = y0 - 1; gy <= y0 + 1; ++gy)
+      wgrad_stage_in<NP>(a, As + (size_t)((gy + 4) & 3) * P::ABYTES, b, gy, x0, tid);
+    wgrad_stage_gout<NP>(a, Bs + (size_t)(y0 & 1) * P::BBYTES, b, y0, x0, tid, bsum);
+    for (int y = y0; y < y1; ++y) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      tc_fence_before();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
 #pragma unroll
-    for (int k = 0; k < P::BITEMS; ++k) {
-      const int idx = tid + k * TC_THREADS;
-      if (idx < a.Cout * P::PG) {
-        const int o = idx / P::PG, pg = idx - o * P::PG;
-        const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
-        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-        bsum[k] += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
-        *reinterpret_cast<uint4*>(Bs + ((size_t)pg * NP + o) * 16) =
-            make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
-                       pack_bf16(v1.z, v1.w));
-      }
-    }
-    // A: for each dy and input channel, 10 input pixels give the three
-    // shifted 8-pixel rows (dx = 0, 1, 2)
-    for (int idx = tid; idx < 3 * a.Cin * P::PG; idx += TC_THREADS) {
-      const int dy = idx / (a.Cin * P::PG), rem2 = idx - dy * a.Cin * P::PG;
-      const int i = rem2 / P::PG, pg = rem2 - i * P::PG;
-      const int gy = y + dy - 1, xs = x0 + 8 * pg;
-      float e[10];
-      if (gy >= 0 && gy < a.H) {
-        const float* src = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W + xs;
-        const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-        const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-        e[0] = xs > 0 ? __ldg(src - 1) : 0.f;
-        e[1] = v0.x; e[2] = v0.y; e[3] = v0.z; e[4] = v0.w;
-        e[5] = v1.x; e[6] = v1.y; e[7] = v1.z; e[8] = v1.w;
-        e[9] = xs + 8 < a.W ? __ldg(src + 8) : 0.f;
-      } else {
+        for (int dy = 0; dy < 3; ++dy) {
+          const uint32_t arow = abase + (uint32_t)(((y + dy - 1 + 4) & 3) * P::ABYTES);
+          const uint32_t brow = bbase + (uint32_t)((y & 1) * P::BBYTES);
 #pragma unroll
-        for (int c = 0; c < 10; ++c) e[c] = 0.f;
-      }
-      uint8_t* dst = As + (size_t)dy * P::ABYTES + ((size_t)pg * 128 + i) * 16;
-#pragma unroll
-      for (int dx = 0; dx < 3; ++dx)   // pixel x0+8pg+j-1+dx = e[j + dx]
-        *reinterpret_cast<uint4*>(dst + (size_t)dx * a.Cin * 16) =
-            make_uint4(pack_bf16(e[dx], e[dx + 1]), pack_bf16(e[dx + 2], e[dx + 3]),
-                       pack_bf16(e[dx + 4], e[dx + 5]), pack_bf16(e[dx + 6], e[dx + 7]));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    tc_fence_before();
-    __syncthreads();
-    if (tid == 0) {
-      tc_fence_after();
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy) {
-#pragma unroll
-        for (int s = 0; s < P::PG / 2; ++s) {
-          const uint64_t ad = mdesc(abase + (uint32_t)(dy * P::ABYTES + (size_t)2 * s * 128 * 16),
-                                    128 * 16, 128);
-          const uint64_t bd = mdesc(bbase + (uint32_t)(2 * s * NP * 16), NP * 16, 128);
-          const uint32_t acc = (first && s == 0) ? 0u : 1u;
-          asm volatile(
-              "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-              " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
-                  tmem + (uint32_t)(dy * NP)),
-              "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-              : "memory");
+          for (int s = 0; s < P::PG / 2; ++s) {
+            const uint64_t ad = mdesc(arow + (uint32_t)(2 * s * 128 * 16), 128 * 16, 128);
+            const uint64_t bd = mdesc(brow + (uint32_t)(2 * s * NP * 16), NP * 16, 128);
+            const uint32_t acc = (first && s == 0) ? 0u : 1u;
+            asm volatile(
+                "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}" ::"r"(
+                    tmem + (uint32_t)(dy * NP)),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                : "memory");
+          }
         }
+        asm volatile(
+            "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                smem_u32(&mbar))
+            : "memory");
       }
-      asm volatile(
-          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-              smem_u32(&mbar))
-          : "memory");
+      first = false;
+      // next rows go to slots no MMA in flight reads: input row y + 2 to the
+      // slot of row y - 2, gout row y + 1 to the other B buffer (row y - 1's)
+      if (y + 1 < y1) {
+        wgrad_stage_in<NP>(a, As + (size_t)((y + 2) & 3) * P::ABYTES, b, y + 2, x0, tid);
+        wgrad_stage_gout<NP>(a, Bs + (size_t)((y + 1) & 1) * P::BBYTES, b, y + 1, x0, tid, bsum);
+      }
+      if (!mbar_wait(smem_u32(&mbar), phase)) {
+        atomicOr(&g_tc_err, 1u);
+        s_fail = 1;
+      }
+      phase ^= 1u;
+      __syncthreads();
+      if (s_fail) break;
     }
-    first = false;
-    if (!mbar_wait(smem_u32(&mbar), phase)) {   // staging buffers are reused next unit
-      atomicOr(&g_tc_err, 1u);
-      s_fail = 1;
-    }
-    phase ^= 1u;
-    tc_fence_before();
     __syncthreads();
-    if (s_fail) break;
   }
   // bias partial of this CTA: item partials through shared memory (the
-  // staging area is free now), summed per channel in pixel-group order
+  // staging area is free: every MMA has completed), summed per channel in
+  // pixel-group order
   float* bred = reinterpret_cast<float*>(sm);
 #pragma unroll
   for (int k = 0; k < P::BITEMS; ++k) {
-    const int idx = tid + k * TC_THREADS;
+    const int idx = tid + k * P::THREADS;
     if (idx < a.Cout * P::PG) bred[idx] = bsum[k];
   }
   __syncthreads();
+  const size_t stride = (size_t)a.Cout * a.Cin * 9 + a.Cout;
   if (tid < a.Cout) {
     float s = 0.f;
     for (int pg = 0; pg < P::PG; ++pg) s += bred[tid * P::PG + pg];
-    a.part[(size_t)blockIdx.x * (a.Cout * a.Cin * 9 + a.Cout) + a.Cout * a.Cin * 9 + tid] = s;
+    a.part[(size_t)blockIdx.x * stride + (size_t)a.Cout * a.Cin * 9 + tid] = s;
   }
-  // epilogue: lane r = dx * Cin + i of warp r / 32, columns dy * NP + o
-  if (!s_fail) {
+  // epilogue (warps 0-3): lane r = dx * Cin + i, columns dy * NP + o
+  if (!s_fail && warp < 4) {
     tc_fence_after();
     const int r = warp * 32 + lane;
     const int dx = r / a.Cin, i = r - dx * a.Cin;
-    float* part = a.part + (size_t)blockIdx.x * (a.Cout * a.Cin * 9 + a.Cout);
+    float* part = a.part + (size_t)blockIdx.x * stride;
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
       uint32_t acc[NP];
@@ -482,24 +522,29 @@ __global__ void k_wgrad_reduce(const float* __restrict__ part, float* __restrict
   else if (gb) gb[e - nw] = s;
 }
 
-int wgrad_grid(int B, int H, int W) {
+// One CTA per SM (the row ring takes ~150 KB of shared memory); rows per
+// unit: about four units per CTA, 4..32 rows.
+void wgrad_plan(int B, int H, int W, int* grid, int* rows_per_unit) {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int nunits = B * H * (W / TC_M);
-  return std::max(1, std::min(nunits, 2 * std::max(sms, 1)));
+  sms = std::max(sms, 1);
+  const long long strips = (long long)B * (W / TC_M);
+  const int ru = (int)std::min<long long>(
+      H, std::max(4LL, std::min(32LL, strips * H / std::max(1LL, 4LL * sms))));
+  const long long nunits = strips * ((H + ru - 1) / ru);
+  *grid = (int)std::max(1LL, std::min(nunits, (long long)sms));
+  *rows_per_unit = ru;
 }
 
 template <int NP>
 cudaError_t launch_wgrad(const WgradTcArgs& a, int grid, cudaStream_t st) {
   using P = WgradTcT<NP>;
+  static_assert(P::SMEM + 1024 > 228 * 1024 / 2, "one CTA per SM keeps TMEM use at NCOLS");
   auto k = k_wgrad_tc<NP>;
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
   if (e) return e;
-  int per_sm = 0;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, TC_THREADS, P::SMEM))) return e;
-  if (per_sm < 1 || per_sm * (int)P::NCOLS > 512) return cudaErrorInvalidConfiguration;
-  k<<<grid, TC_THREADS, P::SMEM, st>>>(a);
+  k<<<grid, P::THREADS, P::SMEM, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -594,7 +639,9 @@ int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W) {
 
 size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W) {
   if (B < 1 || !shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)) return 0;
-  return (size_t)wgrad_grid(B, H, W) * ((size_t)Co * Ci * 9 + Co);
+  int grid = 0, ru = 0;
+  wgrad_plan(B, H, W, &grid, &ru);
+  return (size_t)grid * ((size_t)Co * Ci * 9 + Co);
 }
 
 shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout, float* gw,
@@ -606,8 +653,9 @@ shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout,
     return SHL_EINVAL;
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int grid = wgrad_grid(B, H, W);
-  const WgradTcArgs a{in, gout, ws, B, Ci, Co, H, W};
+  int grid = 0, ru = 0;
+  wgrad_plan(B, H, W, &grid, &ru);
+  const WgradTcArgs a{in, gout, ws, B, Ci, Co, H, W, ru};
   const int np = round16(Co);
   cudaError_t e = np == 16 ? launch_wgrad<16>(a, grid, st)
                 : np == 32 ? launch_wgrad<32>(a, grid, st)

@@ -341,6 +341,22 @@ class _MSE(torch.autograd.Function):
         return ga, None
 
 
+class _ResidualAdd(torch.autograd.Function):
+    """c + h with h overwritten in place (h is a fresh convolution output that
+    nothing saved), the sum done by shl_nn_axpy."""
+
+    @staticmethod
+    def forward(ctx, c, h):
+        c = c.contiguous()
+        _chk("axpy", lib().shl_nn_axpy(_p(c), 1.0, _p(h), h.numel(), _st(h)))
+        ctx.mark_dirty(h)
+        return h
+
+    @staticmethod
+    def backward(ctx, g):
+        return g, g
+
+
 def conv3x3(x, w, b, tc=False):
     """3x3 convolution; tc=True runs the forward, the input gradient and the
     weight gradient on the tensor cores (bfloat16 operands, float32
@@ -465,7 +481,7 @@ class CoeffNet(torch.nn.Module):
     def forward(self, c):
         h = prelu(conv3x3(c, self.w0, self.b0, self.tc), self.a0)
         h = prelu(conv3x3(h, self.w1, self.b1, self.tc), self.a1)
-        return c + conv3x3(h, self.w2, self.b2, self.tc)
+        return _ResidualAdd.apply(c, conv3x3(h, self.w2, self.b2, self.tc))
 
 
 class Adam:
