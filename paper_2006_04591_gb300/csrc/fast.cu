@@ -904,15 +904,21 @@ static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra,
   if (mode == 0 || mode == 1) {
     if (a.nlines == 0) return cudaSuccess;
     const int work = mode == 1 ? ((a.nlines / a.Mh + DEC_FPG - 1) / DEC_FPG) * a.Mh : a.nlines;
-    const int grid = std::min((work + P::NG - 1) / P::NG, sm_count() * 8);
     const size_t sm = P::SMEM_LINES + P::TWB;
+    // persistent grid-stride: exactly the CTAs that fit at once, so that no
+    // partial last wave is left
+    int per_sm = 0;
     if (mode == 0) {
       if ((e = prep(k_lines_fwd<LOG_N>, sm))) return e;
-      k_lines_fwd<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lines_fwd<LOG_N>, P::THREADS, sm);
     } else {
       if ((e = prep(k_dec_lines<LOG_N>, sm))) return e;
-      k_dec_lines<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_lines<LOG_N>, P::THREADS, sm);
     }
+    if (e) return e;
+    const int grid = std::max(1, std::min((work + P::NG - 1) / P::NG, std::max(per_sm, 1) * sm_count()));
+    if (mode == 0) k_lines_fwd<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
+    else k_dec_lines<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
   } else {
     const size_t sm = P::SMEM_LINES + sizeof(float2) * (size_t)P::NG * P::N + P::TWB;
     if ((e = prep(k_rec_lines<LOG_N>, sm))) return e;
