@@ -122,37 +122,61 @@ struct ConvTcT {
   static constexpr uint32_t NCOLS = NP <= 32 ? 32 : 64;       // TMEM columns (power of 2)
 };
 
-// Stage input row gy of image b (zeros outside the image), pixels
-// x0-4..x0+131, as bfloat16 [cg][px][8] into `dst`: one item = 4 pixels x 8
-// channels (8 float4 loads, 4 16-byte stores).
+// Staging of one input row in two halves (global loads into registers, then
+// bfloat16 conversion and shared-memory stores), so that the loads of the
+// next row are in flight while the current row's MMAs and epilogue run.
+// Row gy of image b, pixels x0-4..x0+131 -> bfloat16 [cg][px][8]; one item =
+// 4 pixels x 8 channels (8 float4 loads, 4 16-byte stores); zeros outside the
+// image.
 template <int CG>
-__device__ __forceinline__ void stage_row(const ConvTcArgs& a, uint8_t* dst, int b, int gy, int x0,
-                                          int tid) {
+struct ConvRegs {
+  static constexpr int ITEMS = (CG * (PW / 4) + TC_THREADS - 1) / TC_THREADS;
+  float4 v[ITEMS][8];
+};
+
+template <int CG>
+__device__ __forceinline__ void conv_load_row(const ConvTcArgs& a, ConvRegs<CG>& R, int b, int gy,
+                                              int x0, int tid) {
   constexpr int PG = PW / 4;
   const size_t cs = (size_t)a.H * a.W;
   const bool rok = gy >= 0 && gy < a.H;
-  for (int idx = tid; idx < CG * PG; idx += TC_THREADS) {
+#pragma unroll
+  for (int k = 0; k < ConvRegs<CG>::ITEMS; ++k) {
+    const int idx = tid + k * TC_THREADS;
     const int cg = idx / PG, q = idx - cg * PG;
     const int gx = x0 - 4 + 4 * q;
-    const bool ok = rok && gx >= 0 && gx < a.W;
+    const bool ok = rok && idx < CG * PG && gx >= 0 && gx < a.W;
     const float* src = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W + (ok ? gx : 0);
-    float4 v[8];
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-      v[c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
-                                        : make_float4(0.f, 0.f, 0.f, 0.f);
-    uint8_t* d = dst + ((size_t)cg * PW + 4 * q) * 16;
-    *reinterpret_cast<uint4*>(d) = make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x),
-                                              pack_bf16(v[4].x, v[5].x), pack_bf16(v[6].x, v[7].x));
-    *reinterpret_cast<uint4*>(d + 16) =
-        make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y), pack_bf16(v[4].y, v[5].y),
-                   pack_bf16(v[6].y, v[7].y));
-    *reinterpret_cast<uint4*>(d + 32) =
-        make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z), pack_bf16(v[4].z, v[5].z),
-                   pack_bf16(v[6].z, v[7].z));
-    *reinterpret_cast<uint4*>(d + 48) =
-        make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w), pack_bf16(v[4].w, v[5].w),
-                   pack_bf16(v[6].w, v[7].w));
+      R.v[k][c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
+                                             : make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+}
+
+template <int CG>
+__device__ __forceinline__ void conv_store_row(const ConvRegs<CG>& R, uint8_t* dst, int tid) {
+  constexpr int PG = PW / 4;
+#pragma unroll
+  for (int k = 0; k < ConvRegs<CG>::ITEMS; ++k) {
+    const int idx = tid + k * TC_THREADS;
+    if (idx < CG * PG) {
+      const int cg = idx / PG, q = idx - cg * PG;
+      const float4* v = R.v[k];
+      uint8_t* d = dst + ((size_t)cg * PW + 4 * q) * 16;
+      *reinterpret_cast<uint4*>(d) =
+          make_uint4(pack_bf16(v[0].x, v[1].x), pack_bf16(v[2].x, v[3].x),
+                     pack_bf16(v[4].x, v[5].x), pack_bf16(v[6].x, v[7].x));
+      *reinterpret_cast<uint4*>(d + 16) =
+          make_uint4(pack_bf16(v[0].y, v[1].y), pack_bf16(v[2].y, v[3].y),
+                     pack_bf16(v[4].y, v[5].y), pack_bf16(v[6].y, v[7].y));
+      *reinterpret_cast<uint4*>(d + 32) =
+          make_uint4(pack_bf16(v[0].z, v[1].z), pack_bf16(v[2].z, v[3].z),
+                     pack_bf16(v[4].z, v[5].z), pack_bf16(v[6].z, v[7].z));
+      *reinterpret_cast<uint4*>(d + 48) =
+          make_uint4(pack_bf16(v[0].w, v[1].w), pack_bf16(v[2].w, v[3].w),
+                     pack_bf16(v[4].w, v[5].w), pack_bf16(v[6].w, v[7].w));
+    }
   }
 }
 
@@ -210,13 +234,18 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
   const int runs = (a.H + RU - 1) / RU;
   const int nunits = a.B * tiles_x * runs;
   uint32_t phase = 0;
+  ConvRegs<CG> R;
   for (int u = blockIdx.x; u < nunits && !s_fail; u += gridDim.x) {
     const int b = u / (tiles_x * runs), rem = u - b * tiles_x * runs;
     const int xt = rem / runs, y0 = (rem - xt * runs) * RU, y1 = min(a.H, y0 + RU);
     const int x0 = xt * TC_M;
-    // the three rows of the first output row; the previous unit's MMAs are done
-    for (int gy = y0 - 1; gy <= y0 + 1; ++gy)
-      stage_row<CG>(a, ring + (size_t)((gy + 4) & 3) * P::RBYTES, b, gy, x0, tid);
+    // the three rows of the first output row (the previous unit's MMAs are
+    // done), then the loads of row y0 + 2 start
+    for (int gy = y0 - 1; gy <= y0 + 1; ++gy) {
+      conv_load_row<CG>(a, R, b, gy, x0, tid);
+      conv_store_row<CG>(R, ring + (size_t)((gy + 4) & 3) * P::RBYTES, tid);
+    }
+    if (y0 + 1 < y1) conv_load_row<CG>(a, R, b, y0 + 2, x0, tid);
     for (int y = y0; y < y1; ++y) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // staged rows -> async proxy
       tc_fence_before();
@@ -244,8 +273,12 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
                 smem_u32(&mbar))
             : "memory");
       }
-      // row y + 2 goes to the slot of row y - 2, which no MMA in flight reads
-      if (y + 1 < y1) stage_row<CG>(a, ring + (size_t)((y + 2) & 3) * P::RBYTES, b, y + 2, x0, tid);
+      // row y + 2 (loaded last iteration) goes to the slot of row y - 2, which
+      // no MMA in flight reads; then the loads of row y + 3 start
+      if (y + 1 < y1) {
+        conv_store_row<CG>(R, ring + (size_t)((y + 2) & 3) * P::RBYTES, tid);
+        if (y + 2 < y1) conv_load_row<CG>(a, R, b, y + 3, x0, tid);
+      }
       if (!mbar_wait(smem_u32(&mbar), phase)) {
         atomicOr(&g_tc_err, 1u);
         s_fail = 1;
@@ -304,20 +337,32 @@ struct WgradTcT {
   static constexpr size_t SMEM = SLOTS * ABYTES + 2 * BBYTES;
   static constexpr uint32_t NCOLS = 3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : 256);
   static constexpr int BITEMS = (NP * PG + THREADS - 1) / THREADS;   // gout items per thread
+  static constexpr int IITEMS = (42 * PG + THREADS - 1) / THREADS;   // input items (Cin <= 42)
 };
 
-// Input row gy (zeros outside the image) -> the three shifted copies
-// A[r = dx * Cin + i][p] = in[i][gy][x0 + p + dx - 1], bfloat16 [pg][r][8].
+// Staging of the weight-gradient operands in two halves, so that the global
+// loads of the next rows are in flight while the MMAs of the current row
+// run: *_load fills registers, *_store converts them to bfloat16 and writes
+// shared memory.  Item idx -> (pixel group pg = idx / C, channel idx % C):
+// consecutive threads write consecutive 16-byte rows (no bank conflicts).
 template <int NP>
-__device__ __forceinline__ void wgrad_stage_in(const WgradTcArgs& a, uint8_t* dst, int b, int gy,
-                                               int x0, int tid) {
+struct WgradRegs {
+  float e[WgradTcT<NP>::IITEMS][10];     // input: pixels x0+8pg-1 .. x0+8pg+8
+  float4 g[WgradTcT<NP>::BITEMS][2];     // gout: pixels x0+8pg .. x0+8pg+7
+};
+
+template <int NP>
+__device__ __forceinline__ void wgrad_load_in(const WgradTcArgs& a, WgradRegs<NP>& R, int b, int gy,
+                                              int x0, int tid) {
   using P = WgradTcT<NP>;
   const bool rok = gy >= 0 && gy < a.H;
-  for (int idx = tid; idx < a.Cin * P::PG; idx += P::THREADS) {
-    const int i = idx / P::PG, pg = idx - i * P::PG;
-    const int xs = x0 + 8 * pg;
-    float e[10];
-    if (rok) {
+#pragma unroll
+  for (int k = 0; k < P::IITEMS; ++k) {
+    const int idx = tid + k * P::THREADS;
+    float* e = R.e[k];
+    if (rok && idx < a.Cin * P::PG) {
+      const int pg = idx / a.Cin, i = idx - pg * a.Cin;
+      const int xs = x0 + 8 * pg;
       const float* src = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W + xs;
       const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
       const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
@@ -329,31 +374,59 @@ __device__ __forceinline__ void wgrad_stage_in(const WgradTcArgs& a, uint8_t* ds
 #pragma unroll
       for (int c = 0; c < 10; ++c) e[c] = 0.f;
     }
-    uint8_t* d = dst + ((size_t)pg * 128 + i) * 16;
-#pragma unroll
-    for (int dx = 0; dx < 3; ++dx)   // pixel x0+8pg+j-1+dx = e[j + dx]
-      *reinterpret_cast<uint4*>(d + (size_t)dx * a.Cin * 16) =
-          make_uint4(pack_bf16(e[dx], e[dx + 1]), pack_bf16(e[dx + 2], e[dx + 3]),
-                     pack_bf16(e[dx + 4], e[dx + 5]), pack_bf16(e[dx + 6], e[dx + 7]));
   }
 }
 
-// gout row y -> a B buffer, bfloat16 [pg][o][8], 8 pixels per item (item
-// o * PG + pg, the same for every row, so bsum[k] is this thread's float32
-// bias partial of fixed channels).
+// -> the three shifted copies A[r = dx * Cin + i][p] = in[i][gy][x0 + p + dx - 1]
 template <int NP>
-__device__ __forceinline__ void wgrad_stage_gout(const WgradTcArgs& a, uint8_t* dst, int b, int y,
-                                                 int x0, int tid,
+__device__ __forceinline__ void wgrad_store_in(const WgradTcArgs& a, const WgradRegs<NP>& R,
+                                               uint8_t* dst, int tid) {
+  using P = WgradTcT<NP>;
+#pragma unroll
+  for (int k = 0; k < P::IITEMS; ++k) {
+    const int idx = tid + k * P::THREADS;
+    if (idx < a.Cin * P::PG) {
+      const int pg = idx / a.Cin, i = idx - pg * a.Cin;
+      const float* e = R.e[k];
+      uint8_t* d = dst + ((size_t)pg * 128 + i) * 16;
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx)   // pixel x0+8pg+j-1+dx = e[j + dx]
+        *reinterpret_cast<uint4*>(d + (size_t)dx * a.Cin * 16) =
+            make_uint4(pack_bf16(e[dx], e[dx + 1]), pack_bf16(e[dx + 2], e[dx + 3]),
+                       pack_bf16(e[dx + 4], e[dx + 5]), pack_bf16(e[dx + 6], e[dx + 7]));
+    }
+  }
+}
+
+template <int NP>
+__device__ __forceinline__ void wgrad_load_gout(const WgradTcArgs& a, WgradRegs<NP>& R, int b,
+                                                int y, int x0, int tid) {
+  using P = WgradTcT<NP>;
+#pragma unroll
+  for (int k = 0; k < P::BITEMS; ++k) {
+    const int idx = tid + k * P::THREADS;
+    if (idx < a.Cout * P::PG) {
+      const int pg = idx / a.Cout, o = idx - pg * a.Cout;
+      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
+      R.g[k][0] = __ldg(reinterpret_cast<const float4*>(src));
+      R.g[k][1] = __ldg(reinterpret_cast<const float4*>(src + 4));
+    }
+  }
+}
+
+// -> B[o][p] = gout[o][y][x0 + p]; bsum[k] gathers this thread's float32
+// bias partial (item k always has channel (tid + k THREADS) mod Cout)
+template <int NP>
+__device__ __forceinline__ void wgrad_store_gout(const WgradTcArgs& a, const WgradRegs<NP>& R,
+                                                 uint8_t* dst, int tid,
                                                  float (&bsum)[WgradTcT<NP>::BITEMS]) {
   using P = WgradTcT<NP>;
 #pragma unroll
   for (int k = 0; k < P::BITEMS; ++k) {
     const int idx = tid + k * P::THREADS;
     if (idx < a.Cout * P::PG) {
-      const int o = idx / P::PG, pg = idx - o * P::PG;
-      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
-      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
+      const int pg = idx / a.Cout, o = idx - pg * a.Cout;
+      const float4 v0 = R.g[k][0], v1 = R.g[k][1];
       bsum[k] += ((v0.x + v0.y) + (v0.z + v0.w)) + ((v1.x + v1.y) + (v1.z + v1.w));
       *reinterpret_cast<uint4*>(dst + ((size_t)pg * NP + o) * 16) =
           make_uint4(pack_bf16(v0.x, v0.y), pack_bf16(v0.z, v0.w), pack_bf16(v1.x, v1.y),
@@ -407,15 +480,24 @@ __global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcAr
   float bsum[P::BITEMS];   // bias partials of this thread's fixed gout items, float32
 #pragma unroll
   for (int k = 0; k < P::BITEMS; ++k) bsum[k] = 0.f;
+  WgradRegs<NP> R;
 
   for (int u = blockIdx.x; u < nunits && !s_fail; u += gridDim.x) {
     const int b = u / (tiles_x * runs), rem = u - b * tiles_x * runs;
     const int xt = rem / runs, y0 = (rem - xt * runs) * RU, y1 = min(a.H, y0 + RU);
     const int x0 = xt * TC_M;
-    // the previous unit's MMAs are done: stage rows y0-1..y0+1 and gout row y0
-    for (int gy = y0 - 1; gy <= y0 + 1; ++gy)
-      wgrad_stage_in<NP>(a, As + (size_t)((gy + 4) & 3) * P::ABYTES, b, gy, x0, tid);
-    wgrad_stage_gout<NP>(a, Bs + (size_t)(y0 & 1) * P::BBYTES, b, y0, x0, tid, bsum);
+    // the previous unit's MMAs are done: stage rows y0-1..y0+1 and gout row
+    // y0, then start the loads of input row y0+2 and gout row y0+1
+    for (int gy = y0 - 1; gy <= y0 + 1; ++gy) {
+      wgrad_load_in<NP>(a, R, b, gy, x0, tid);
+      wgrad_store_in<NP>(a, R, As + (size_t)((gy + 4) & 3) * P::ABYTES, tid);
+    }
+    wgrad_load_gout<NP>(a, R, b, y0, x0, tid);
+    wgrad_store_gout<NP>(a, R, Bs + (size_t)(y0 & 1) * P::BBYTES, tid, bsum);
+    if (y0 + 1 < y1) {
+      wgrad_load_in<NP>(a, R, b, y0 + 2, x0, tid);
+      wgrad_load_gout<NP>(a, R, b, y0 + 1, x0, tid);
+    }
     for (int y = y0; y < y1; ++y) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       tc_fence_before();
@@ -445,11 +527,16 @@ __global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcAr
             : "memory");
       }
       first = false;
-      // next rows go to slots no MMA in flight reads: input row y + 2 to the
-      // slot of row y - 2, gout row y + 1 to the other B buffer (row y - 1's)
+      // the rows loaded last iteration go to slots no MMA in flight reads:
+      // input row y + 2 to the slot of row y - 2, gout row y + 1 to the other
+      // B buffer (row y - 1's); then the loads of the rows after them start
       if (y + 1 < y1) {
-        wgrad_stage_in<NP>(a, As + (size_t)((y + 2) & 3) * P::ABYTES, b, y + 2, x0, tid);
-        wgrad_stage_gout<NP>(a, Bs + (size_t)((y + 1) & 1) * P::BBYTES, b, y + 1, x0, tid, bsum);
+        wgrad_store_in<NP>(a, R, As + (size_t)((y + 2) & 3) * P::ABYTES, tid);
+        wgrad_store_gout<NP>(a, R, Bs + (size_t)((y + 1) & 1) * P::BBYTES, tid, bsum);
+        if (y + 2 < y1) {
+          wgrad_load_in<NP>(a, R, b, y + 3, x0, tid);
+          wgrad_load_gout<NP>(a, R, b, y + 2, x0, tid);
+        }
       }
       if (!mbar_wait(smem_u32(&mbar), phase)) {
         atomicOr(&g_tc_err, 1u);
@@ -472,9 +559,9 @@ __global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcAr
   }
   __syncthreads();
   const size_t stride = (size_t)a.Cout * a.Cin * 9 + a.Cout;
-  if (tid < a.Cout) {
+  if (tid < a.Cout) {   // items of channel o: idx = pg * Cout + o
     float s = 0.f;
-    for (int pg = 0; pg < P::PG; ++pg) s += bred[tid * P::PG + pg];
+    for (int pg = 0; pg < P::PG; ++pg) s += bred[pg * a.Cout + tid];
     a.part[(size_t)blockIdx.x * stride + (size_t)a.Cout * a.Cin * 9 + tid] = s;
   }
   // epilogue (warps 0-3): lane r = dx * Cin + i, columns dy * NP + o
@@ -555,9 +642,13 @@ cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P::SMEM);
   if (e) return e;
   // CTAs per SM for the grid size: the shared-memory bound (228 KB per SM,
-  // 1 KB reserved per CTA), at most 8 and at most 512 TMEM columns.  No CTA
+  // 1 KB reserved per CTA) and the register bound, at most 8 and at most 512
+  // TMEM columns.  No CTA
   // waits on another, so the count only sizes the grid.
   int per_sm = (int)((228u * 1024u) / (P::SMEM + 1024u + 256u));
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.numRegs > 0)
+    per_sm = std::min(per_sm, 65536 / (fa.numRegs * TC_THREADS));
   per_sm = std::max(1, std::min({per_sm, 8, (int)(512 / P::NCOLS)}));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
