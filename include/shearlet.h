@@ -102,6 +102,19 @@ shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_le
                            int full, int device, shl_bank** out);
 
 /*
+ * shl_bank_create_gpu - shl_bank_create with the construction on `device`
+ * (float64 throughout: one CTA per filter column builds the column spectrum,
+ * its inverse DFT along w2, the digital-shear multiplier of Eqs. 2.4-2.5 and
+ * the forward DFT; then the even part, W, RMS and the float32 tables).  The
+ * result is the bank shl_bank_create builds, to float64 rounding (the host
+ * copies read by shl_bank_copy_info are downloaded).  The paper times this
+ * construction as its first experiment (filters on the GPU vs the CPU).
+ * device >= 0; errors as shl_bank_create.
+ */
+shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shear_levels,
+                               int full, int device, shl_bank** out);
+
+/*
  * shl_bank_create_from_spectra - use caller-supplied spectra (Sec. 3.4: any
  * filter tensor ``tfshearlets`` of shape [1, N, M, K]).
  *   spectra  host float64 [K][rows][cols], natural order, real.  Each must

@@ -155,6 +155,17 @@ void free_bank(shl_bank* b) {
   delete b;
 }
 
+// exp(-2 pi i q / TW_P), q < TW_P, computed in float64 and rounded.
+std::vector<float2> twiddle_table() {
+  std::vector<float2> hT(shl::TW_P);
+  const double PI = 3.14159265358979323846264338327950288;
+  for (int q = 0; q < shl::TW_P; ++q) {
+    const double a = -2.0 * PI * q / shl::TW_P;
+    hT[q] = make_float2((float)std::cos(a), (float)std::sin(a));
+  }
+  return hT;
+}
+
 shl_status upload_bank(shl_bank* b) {
   const int N = b->N, M = b->M, Mh = b->Mh, K = b->K;
   const bool host_only = b->device < 0;
@@ -180,12 +191,7 @@ shl_status upload_bank(shl_bank* b) {
   for (int y = 0; y < N; ++y)
     for (int x = 0; x < Mh; ++x) hW[(size_t)x * N + y] = (float)(1.0 / b->dual_w[(size_t)y * M + x]);
   for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
-  std::vector<float2> hT(shl::TW_P);
-  const double PI = 3.14159265358979323846264338327950288;
-  for (int q = 0; q < shl::TW_P; ++q) {
-    const double a = -2.0 * PI * q / shl::TW_P;
-    hT[q] = make_float2((float)std::cos(a), (float)std::sin(a));
-  }
+  const std::vector<float2> hT = twiddle_table();
   DevGuard g(b->device);
   if (cudaMalloc(&b->dG, hG.size() * sizeof(float)) != cudaSuccess ||
       cudaMalloc(&b->dInvW, hW.size() * sizeof(float)) != cudaSuccess ||
@@ -496,6 +502,77 @@ shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_le
   b->idx = std::move(hb.idx);
   s = upload_bank(b);
   if (s != SHL_OK) { free_bank(b); return s; }
+  *out = b;
+  return SHL_OK;
+}
+
+shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shear_levels,
+                               int full, int device, shl_bank** out) {
+  if (!out) return fail(SHL_EINVAL, "out is NULL");
+  *out = nullptr;
+  shl_status s = check_size(rows, cols);
+  if (s != SHL_OK) return s;
+  if (device < 0) return fail(SHL_EINVAL, "shl_bank_create_gpu needs a device >= 0");
+  std::vector<shl::BankItem> items;
+  const char* err = shl::bank_items(n_scales, shear_levels, full, &items);
+  if (*err) return fail(SHL_EINVAL, err);
+  const int N = rows, M = cols, Mh = M / 2 + 1, K = (int)items.size();
+  const size_t plane = (size_t)N * M;
+  DevGuard g(device);
+  shl_bank* b = new shl_bank;
+  b->device = device; b->N = N; b->M = M; b->Mh = Mh; b->K = K;
+  b->idx.assign((size_t)K * 3, 0);
+  for (int i = 0; i < K; ++i) {
+    b->idx[3 * i] = items[i].cone;
+    b->idx[3 * i + 1] = items[i].scale;
+    b->idx[3 * i + 2] = items[i].k;
+  }
+  double *dS = nullptr, *dT = nullptr, *dW = nullptr, *dR = nullptr;
+  unsigned* dBad = nullptr;
+  auto cleanup = [&]() {
+    if (dS) cudaFree(dS);
+    if (dT) cudaFree(dT);
+    if (dW) cudaFree(dW);
+    if (dR) cudaFree(dR);
+    if (dBad) cudaFree(dBad);
+  };
+  if (cudaMalloc(&dS, sizeof(double) * K * plane) || cudaMalloc(&dT, sizeof(double) * plane) ||
+      cudaMalloc(&dW, sizeof(double) * plane) || cudaMalloc(&dR, sizeof(double) * K) ||
+      cudaMalloc(&dBad, sizeof(unsigned)) ||
+      cudaMalloc(&b->dG, sizeof(float) * (size_t)K * Mh * N) ||
+      cudaMalloc(&b->dInvW, sizeof(float) * (size_t)Mh * N) ||
+      cudaMalloc(&b->dTw, sizeof(float2) * shl::TW_P) ||
+      cudaMalloc(&b->dRms, sizeof(float) * K)) {
+    cudaGetLastError();
+    cleanup();
+    free_bank(b);
+    return fail(SHL_ENOMEM, "cudaMalloc failed for the filter bank");
+  }
+  cudaError_t e = shl::build_bank_device(rows, cols, n_scales, shear_levels, full, items, dS, dT, dW,
+                                         dR, b->dG, b->dInvW, dBad, nullptr);
+  unsigned bad = 0;
+  b->spectra.resize((size_t)K * plane);
+  b->dual_w.resize(plane);
+  b->rms.resize(K);
+  if (!e) e = cudaMemcpy(&bad, dBad, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(b->rms.data(), dR, sizeof(double) * K, cudaMemcpyDeviceToHost);
+  if (!e) e = cudaMemcpy(b->dual_w.data(), dW, sizeof(double) * plane, cudaMemcpyDeviceToHost);
+  if (!e)
+    e = cudaMemcpy(b->spectra.data(), dS, sizeof(double) * K * plane, cudaMemcpyDeviceToHost);
+  const std::vector<float2> hT = twiddle_table();
+  std::vector<float> hR(K);
+  for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
+  if (!e) e = cudaMemcpy(b->dTw, hT.data(), sizeof(float2) * hT.size(), cudaMemcpyHostToDevice);
+  if (!e) e = cudaMemcpy(b->dRms, hR.data(), sizeof(float) * K, cudaMemcpyHostToDevice);
+  cleanup();
+  if (e) {
+    free_bank(b);
+    return cuda_fail(e, "shl_bank_create_gpu");
+  }
+  if (bad) {
+    free_bank(b);
+    return fail(SHL_EINVAL, "dual frame weights W = sum G_i^2 must be > 0");
+  }
   *out = b;
   return SHL_OK;
 }

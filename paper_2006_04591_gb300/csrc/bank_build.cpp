@@ -160,27 +160,35 @@ std::vector<double> cone1(const Filters& F, int j, int J, int l, int k, int Nr, 
   return ev;
 }
 
-struct Item { int cone, scale, k, l; };
-
 }  // namespace
+
+void maxflat_coeffs(double b[5]) {
+  const Filters F;
+  for (int m = 0; m < 5; ++m) b[m] = F.b[m];
+}
+
+const char* bank_items(int n_scales, const int* shear_levels, int full,
+                       std::vector<BankItem>* items) {
+  static thread_local std::string err;
+  if (n_scales < 1 || n_scales > 8) return (err = "n_scales must be in [1, 8]").c_str();
+  items->clear();
+  items->push_back({0, 0, 0, 0});
+  for (int j = 0; j < n_scales; ++j) {
+    const int l = shear_levels ? shear_levels[j] : (j + 2) / 2;   // ceil((j+1)/2)
+    if (l < 0 || l > 4) return (err = "shear levels must be in [0, 4]").c_str();
+    const int kmax1 = 1 << l, kmax2 = full ? (1 << l) : (1 << l) - 1;
+    for (int k = -kmax1; k <= kmax1; ++k) items->push_back({1, j + 1, k, l});
+    for (int k = -kmax2; k <= kmax2; ++k) items->push_back({2, j + 1, k, l});
+  }
+  return "";
+}
 
 const char* build_shearlet_bank(int rows, int cols, int n_scales, const int* shear_levels,
                                 int full, HostBank* out) {
-  static thread_local std::string err;
-  if (n_scales < 1 || n_scales > 8) return (err = "n_scales must be in [1, 8]").c_str();
-  std::vector<int> lv(n_scales);
-  for (int j = 0; j < n_scales; ++j) {
-    lv[j] = shear_levels ? shear_levels[j] : (j + 2) / 2;   // ceil((j+1)/2)
-    if (lv[j] < 0 || lv[j] > 4) return (err = "shear levels must be in [0, 4]").c_str();
-  }
+  std::vector<BankItem> items;
+  const char* e = bank_items(n_scales, shear_levels, full, &items);
+  if (*e) return e;
   const int J = n_scales, N = rows, M = cols;
-  std::vector<Item> items;
-  items.push_back({0, 0, 0, 0});
-  for (int j = 0; j < J; ++j) {
-    const int l = lv[j], kmax1 = 1 << l, kmax2 = full ? (1 << l) : (1 << l) - 1;
-    for (int k = -kmax1; k <= kmax1; ++k) items.push_back({1, j + 1, k, l});
-    for (int k = -kmax2; k <= kmax2; ++k) items.push_back({2, j + 1, k, l});
-  }
   const int K = (int)items.size();
   Filters F;
   out->rows = N; out->cols = M; out->K = K;
@@ -193,7 +201,7 @@ const char* build_shearlet_bank(int rows, int cols, int n_scales, const int* she
   }
   auto work = [&](int i) {
     double* dst = out->spectra.data() + (size_t)i * N * M;
-    const Item& it = items[i];
+    const BankItem& it = items[i];
     if (it.cone == 0) {
       for (int p2 = 0; p2 < N; ++p2)
         for (int p1 = 0; p1 < M; ++p1)

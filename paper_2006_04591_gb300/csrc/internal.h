@@ -61,6 +61,23 @@ shl_status decompose_staged(const shl_bank* b, const float* x, int batch, void* 
                             shl_dtype dtype, int flags, void* ws, size_t ws_bytes, void* stream,
                             int stage_subbands_max);
 
+// Filters of a bank in order: cone 0 (low-pass), then per scale cone 1
+// (k = -2^l..2^l) and cone 2 (k = -(2^l-1)..2^l-1, or +-2^l when full).
+struct BankItem { int cone, scale, k, l; };
+const char* bank_items(int n_scales, const int* shear_levels, int full,
+                       std::vector<BankItem>* items);
+// Coefficients b_0..b_4 of the maximally flat low-pass H(w) = b0 + sum b_m cos(m w).
+void maxflat_coeffs(double b[5]);
+
+// float64 construction on the current device (bank_gpu.cu): spectra
+// [K][N][M] natural order into d_spectra (d_tmp: one [N][M] plane of
+// scratch), W [N][M], RMS [K], and the float32 tables of the transform
+// (G [K][Mh][N], 1/W [Mh][N]); *d_bad counts points with W <= 0.
+cudaError_t build_bank_device(int rows, int cols, int n_scales, const int* shear_levels, int full,
+                              const std::vector<BankItem>& items, double* d_spectra,
+                              double* d_tmp, double* d_w, double* d_rms, float* d_G,
+                              float* d_invW, unsigned* d_bad, cudaStream_t st);
+
 // Host float64 filter-bank construction (bank_build.cpp).
 struct HostBank {
   int rows = 0, cols = 0, K = 0;

@@ -14,8 +14,9 @@ on the device, L2 flushed between timed repetitions), shearlet coefficients
 per second, algorithmic HBM bytes per second (images and coefficients once
 per direction, float32 half-spectrum filters once per direction) and its
 fraction of the measured copy bandwidth.  Also the denoising time and PSNR
-at 16 x 512 x 512 and the differentiable layer's forward + backward time at
-32 x 256 x 256 with bfloat16 coefficients.
+at 16 x 512 x 512, the differentiable layer's forward + backward time at
+32 x 256 x 256 with bfloat16 coefficients, and the filter-bank construction
+time on the host and on the GPU.
 """
 
 from __future__ import annotations
@@ -96,6 +97,26 @@ def small_case(N, B):
         raise SystemExit("perfect reconstruction failed")
 
 
+def bank_point(N, J, reps=3):
+    """Wall time of the filter-bank construction: host float64 builder +
+    upload (shl_bank_create) against the GPU builder (shl_bank_create_gpu)."""
+    import time
+    out = {"rows": N, "cols": N, "scales": J}
+    for name, gpu in (("host_s", False), ("gpu_s", True)):
+        Bank.create(N, N, J, device=0, on_gpu=gpu).close()          # warm-up
+        best = 1e30
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            b = Bank.create(N, N, J, device=0, on_gpu=gpu)
+            torch.cuda.synchronize()
+            best = min(best, time.perf_counter() - t0)
+            b.close()
+        out[name] = best
+    out["filters"] = Bank.create(N, N, J, device=0, on_gpu=True).K
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
@@ -106,7 +127,9 @@ def main():
     if args.case:
         small_case(*args.case)
         return
-    res = {"transform": [], "denoise": None, "layer": None}
+    res = {"transform": [], "denoise": None, "layer": None, "bank": []}
+    for N, J in ((256, 2), (512, 4), (1024, 4)):
+        res["bank"].append(bank_point(N, J))
     b256_2 = Bank.create(256, 256, 2, device=0)
     res["transform"].append(dict(transform_point(b256_2, 1, torch.float32), config="plain 256, K=17"))
     b512 = Bank.create(512, 512, 4, device=0)

@@ -56,6 +56,7 @@ def lib():
         "shl_last_error_detail": (ctypes.c_char_p, []),
         "shl_bank_create": (i, [i, i, i, vp, i, i, P(vp)]),
         "shl_bank_create_from_spectra": (i, [i, i, i, vp, vp, i, P(vp)]),
+        "shl_bank_create_gpu": (i, [i, i, i, vp, i, i, P(vp)]),
         "shl_bank_destroy": (i, [vp]),
         "shl_bank_query": (i, [vp, P(i), P(i), P(i)]),
         "shl_bank_copy_info": (i, [vp, vp, vp, vp, vp]),
@@ -129,6 +130,17 @@ def shl_bank_create(rows, cols, n_scales, shear_levels=None, full=0, device=0):
         lv = ctypes.cast(arr, ctypes.c_void_p)
     _check("shl_bank_create", lib().shl_bank_create(rows, cols, n_scales, lv, int(full), device,
                                                     ctypes.byref(h)))
+    return h
+
+
+def shl_bank_create_gpu(rows, cols, n_scales, shear_levels=None, full=0, device=0):
+    h = ctypes.c_void_p()
+    lv = None
+    if shear_levels is not None:
+        arr = (ctypes.c_int * len(shear_levels))(*shear_levels)
+        lv = ctypes.cast(arr, ctypes.c_void_p)
+    _check("shl_bank_create_gpu", lib().shl_bank_create_gpu(rows, cols, n_scales, lv, int(full),
+                                                            device, ctypes.byref(h)))
     return h
 
 
@@ -249,8 +261,11 @@ class Bank:
         self._rms_dev = None
 
     @classmethod
-    def create(cls, rows, cols, n_scales, shear_levels=None, full=False, device=0):
-        return cls(shl_bank_create(rows, cols, n_scales, shear_levels, full, device), device)
+    def create(cls, rows, cols, n_scales, shear_levels=None, full=False, device=0, on_gpu=False):
+        """Build the digital shearlet system; on_gpu=True constructs it on the
+        device (shl_bank_create_gpu), else on the host (shl_bank_create)."""
+        make = shl_bank_create_gpu if on_gpu else shl_bank_create
+        return cls(make(rows, cols, n_scales, shear_levels, full, device), device)
 
     @classmethod
     def from_spectra(cls, spectra, idx=None, device=0):
