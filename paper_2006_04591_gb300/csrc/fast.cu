@@ -568,12 +568,26 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
   float2 acc[R];
 #pragma unroll
   for (int u = 0; u < R; ++u) acc[u] = make_float2(0.f, 0.f);
-  for (int s = s_begin + g; s < s_end; s += NG) {
+  // Each group's row of `red` (free until the reduction below) holds the
+  // next staged line, fetched with cp.async while the current one is
+  // transformed.
+  float2* pre = red + (size_t)g * N;
+  auto fetch = [&](int s) {
     const float2* U = a.stage + ((size_t)(s - a.s0) * a.Mh + kx) * N;
+    for (int c = j; c < N / 2; c += T) cp_async16(pre + 2 * c, U + 2 * c);
+  };
+  if (s_begin + g < s_end) fetch(s_begin + g);
+  cp_async_commit();
+  for (int s = s_begin + g; s < s_end; s += NG) {
     const float* G = a.G + ((size_t)(s - b * a.K) * a.Mh + kx) * N;
+    cp_async_wait0();                       // this lane's copies of line s
+    group_sync<T>(1 + g);                   // ... and the whole group's
     float2 v[R];
 #pragma unroll
-    for (int u = 0; u < R; ++u) v[u] = U[j + u * T];
+    for (int u = 0; u < R; ++u) v[u] = pre[j + u * T];
+    group_sync<T>(1 + g);                   // line read before it is overwritten
+    if (s + NG < s_end) fetch(s + NG);
+    cp_async_commit();
     line_fft<N, R, -1>(v, line, j, 1 + g, twl);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
@@ -582,6 +596,8 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
       acc[u].y = fmaf(gv, v[u].y, acc[u].y);
     }
   }
+  cp_async_wait0();
+  group_sync<T>(1 + g);                     // no copy into this row is pending
 #pragma unroll
   for (int u = 0; u < R; ++u) red[(size_t)g * N + j + u * T] = acc[u];
   __syncthreads();
