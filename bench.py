@@ -303,8 +303,12 @@ def run_gpu(args):
     for _ in range(3):
         e2e_step()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     e2e_times = timed(e2e_step, args.steps)
-    t_e2e = sum(e2e_times) / len(e2e_times) / 1e3
+    t_e2e = reduce_max_time(sum(e2e_times) / len(e2e_times) / 1e3, dist if world > 1 else None, dev)
+    if world > 1:
+        dist.barrier()
     clock_info = clocks.stop()
     clock_info["window"] = "timed, per-kernel-event and end-to-end passes"
 
