@@ -127,7 +127,7 @@ def main():
     if args.case:
         small_case(*args.case)
         return
-    res = {"transform": [], "denoise": None, "layer": None, "bank": []}
+    res = {"transform": [], "denoise": None, "layer": None, "bank": [], "inpainting": []}
     for N, J in ((256, 2), (512, 4), (1024, 4)):
         res["bank"].append(bank_point(N, J))
     b256_2 = Bank.create(256, 256, 2, device=0)
@@ -149,6 +149,19 @@ def main():
     res["denoise"] = {"batch": 16, "size": 512, "filters": 49, "ms": t * 1e3,
                       "psnr_noisy": apps.psnr(xn, ct).mean().item(),
                       "psnr_denoised": apps.psnr(den, ct).mean().item()}
+    # inpainting as in the paper's experiments: 512 x 512, 50 iterations of
+    # the hard-threshold iteration, random and squared masks (8 images each)
+    for kind in ("random", "squared"):
+        clean8, mask8, masked8 = synth.inpaint_batch(8, 512, 0.5, seed0=2000, kind=kind)
+        fm = torch.from_numpy(masked8.astype(np.float32)).cuda()
+        mk = torch.from_numpy(mask8.astype(np.float32)).cuda()
+        c8 = torch.from_numpy(clean8.astype(np.float32)).cuda()
+        t = _time(lambda: apps.iht_inpaint(b512, fm, mk, 50), reps=3)
+        out = apps.iht_inpaint(b512, fm, mk, 50)
+        res["inpainting"].append({"mask": kind, "batch": 8, "size": 512, "filters": 49,
+                                  "iterations": 50, "ms": t * 1e3,
+                                  "psnr_masked": apps.psnr(fm, c8).mean().item(),
+                                  "psnr_inpainted": apps.psnr(out, c8).mean().item()})
     # differentiable layer, 32 x 256, 33 filters, bfloat16 coefficients
     b256_3 = Bank.create(256, 256, 3, device=0)
     c32, n32 = synth.denoise_batch(32, 256, sigma, seed0=1000)

@@ -21,6 +21,10 @@ Recipes (``numpy.random.default_rng(seed)``, PCG64):
   integer frequency vectors of norm in [8, 32] and phi_q ~ U[0, 2 pi).
 * ``cartoon_texture``: ``clip(cartoon + texture, 0, 1)``.
 * ``bernoulli_mask``: i.i.d. keep-probability p (1 = observed pixel).
+* ``square_mask``: the "squared" occlusion pattern of the inpainting
+  experiments (whose exact layout the paper does not give): U{count}
+  axis-aligned squares of side U{N/32..N/8}, top-left corners U[0, N-side]^2,
+  set to 0 (missing); about 16 % of the pixels at the defaults.
 * ``gaussian_noise``: i.i.d. N(0, sigma^2).
 """
 
@@ -127,6 +131,18 @@ def bernoulli_mask(n: int, m: int | None = None, p: float = 0.5, seed: int = 0):
     return (rng.uniform(size=(n, m)) < p).astype(np.float64)
 
 
+def square_mask(n: int, m: int | None = None, count: int = 24, seed: int = 0):
+    m = n if m is None else m
+    rng = np.random.default_rng(seed)
+    mask = np.ones((n, m), np.float64)
+    for _ in range(count):
+        side = int(rng.integers(max(1, min(n, m) // 32), max(2, min(n, m) // 8) + 1))
+        y = int(rng.integers(0, n - side + 1))
+        x = int(rng.integers(0, m - side + 1))
+        mask[y:y + side, x:x + side] = 0.0
+    return mask
+
+
 def gaussian_noise(shape, sigma: float, seed: int = 0):
     rng = np.random.default_rng(seed)
     return sigma * rng.standard_normal(shape)
@@ -152,8 +168,13 @@ def denoise_batch(b: int = 16, n: int = 512, sigma: float = 30 / 255,
     return clean, noisy
 
 
-def inpaint_batch(b: int = 8, n: int = 512, p: float = 0.5, seed0: int = 2000):
-    """Cartoon+texture images, Bernoulli masks and masked images."""
+def inpaint_batch(b: int = 8, n: int = 512, p: float = 0.5, seed0: int = 2000,
+                  kind: str = "random"):
+    """Cartoon+texture images, masks (``random``: Bernoulli(p) keep; ``squared``:
+    square holes) and masked images."""
     clean = np.stack([cartoon_texture(n, n, seed0 + i) for i in range(b)])
-    mask = np.stack([bernoulli_mask(n, n, p, 50_000 + seed0 + i) for i in range(b)])
+    if kind == "squared":
+        mask = np.stack([square_mask(n, n, seed=60_000 + seed0 + i) for i in range(b)])
+    else:
+        mask = np.stack([bernoulli_mask(n, n, p, 50_000 + seed0 + i) for i in range(b)])
     return clean, mask, clean * mask
