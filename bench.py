@@ -185,6 +185,58 @@ def _oracle_sample(seconds_target=12.0, max_images=B_IMG):
     return done, dt
 
 
+# ------------------------------------------------- CPU table (oracle only)
+_TABLE_BANK = {}
+
+
+def _table_init(n, J):
+    from oracle import bank as Bk
+    _TABLE_BANK["ref"] = Bk.shearlet_bank(n, n, J)
+
+
+def _table_work(args):
+    """dec + rec of one seeded cartoon with the worker's oracle bank."""
+    import numpy as np
+    from oracle import transform as OT
+    from paper_2006_04591_gb300 import synth
+    n, seed = args
+    ref = _TABLE_BANK["ref"]
+    x = synth.cartoon(n, n, seed).astype(np.float32)
+    c = OT.decompose(x, ref["psi_hat"]).real
+    OT.reconstruct(c, ref["psi_hat"])
+    return 0
+
+
+def run_cpu_table():
+    """The FP64 oracle (numpy float64, single-threaded FFTs) on the host cores
+    for the plain-transform, metric and 1024 x 1024 workloads: one process,
+    and a spawn process pool over the images (bank built in each worker
+    before the timed pass).  Prints one JSON line."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    cores = os.cpu_count() or 1
+    rows = []
+    for n, J, B in ((256, 2, 1), (512, 4, 16), (1024, 4, 1), (1024, 4, 8)):
+        _table_init(n, J)
+        seeds = [(n, 100 + b) for b in range(B)]
+        t0 = time.perf_counter()
+        for a in seeds:
+            _table_work(a)
+        t1 = time.perf_counter() - t0
+        row = {"rows": n, "scales": J, "batch": B, "one_process_s": t1}
+        if B > 1:
+            nw = min(cores, B)
+            with ctx.Pool(nw, initializer=_table_init, initargs=(n, J)) as pool:
+                pool.map(_table_work, seeds, chunksize=1)          # workers up, banks built
+                t0 = time.perf_counter()
+                pool.map(_table_work, seeds, chunksize=1)
+                row["all_cores_s"] = time.perf_counter() - t0
+                row["processes"] = nw
+        rows.append(row)
+    print(json.dumps({"cpu_table": rows, "cores": cores, "kind": "oracle (numpy float64)"}))
+    return 0
+
+
 def _cpu_cores_used():
     # numpy.fft (pocketfft) runs on one thread; the oracle loops in Python.
     return 1
@@ -389,9 +441,13 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-table", action="store_true",
+                    help="time the FP64 oracle at several workloads on the host cores and exit")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.cpu_table:
+        return run_cpu_table()
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)
