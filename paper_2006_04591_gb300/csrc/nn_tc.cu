@@ -11,8 +11,9 @@
 // address moved by dx * 16 bytes: no im2col copy.  The weights sit in the
 // same layout [tap][ci/8][n][8 ci] for the whole launch.  One thread issues
 // the 9 * Ci/16 MMAs (M = 128, N = Cout padded to 16, K = 16) into a TMEM
-// accumulator and commits them to an mbarrier; the four warps then read
-// their 32 TMEM lanes (= pixels) and store the NCHW output rows.  The wait
+// accumulator and commits them to an mbarrier; warps w and w + 4 then read
+// TMEM lanes 32 (w % 4) .. + 31 (= pixels), each one half of the columns
+// (= output channels), and store the NCHW output rows.  The wait
 // on the mbarrier is bounded: when it runs out the kernel records the
 // error (read by shl_nn_tc_status), frees its TMEM and returns.
 #include <cuda_bf16.h>
@@ -28,7 +29,7 @@ namespace {
 __device__ unsigned int g_tc_err = 0;
 
 constexpr int TC_M = 128;            // output pixels per tile (MMA M)
-constexpr int TC_THREADS = 128;      // four warps: one per 32 TMEM lanes
+constexpr int CONV_THREADS = 256;    // warps w and w + 4 share TMEM lanes 32 (w % 4)
 // Staged pixels per row: x0 - 4 .. x0 + 131, in float4 groups aligned to 16
 // bytes (x0 and W are multiples of 128, so each group lies wholly inside or
 // wholly outside the image); output pixel m, tap dx reads staged pixel
@@ -111,6 +112,13 @@ __device__ __forceinline__ void tc_fence_after() {
       : "r"(ADDR)                                                                           \
       : "memory")
 
+#define SHL_TMEM_LD8(R, ADDR)                                                               \
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"      \
+               : "=r"((R)[0]), "=r"((R)[1]), "=r"((R)[2]), "=r"((R)[3]), "=r"((R)[4]),         \
+                 "=r"((R)[5]), "=r"((R)[6]), "=r"((R)[7])                                      \
+               : "r"(ADDR)                                                                     \
+               : "memory")
+
 template <int CG, int NP>
 struct ConvTcT {
   static_assert(CG % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 64, "tile shape");
@@ -130,7 +138,7 @@ struct ConvTcT {
 // image.
 template <int CG>
 struct ConvRegs {
-  static constexpr int ITEMS = (CG * (PW / 4) + TC_THREADS - 1) / TC_THREADS;
+  static constexpr int ITEMS = (CG * (PW / 4) + CONV_THREADS - 1) / CONV_THREADS;
   float4 v[ITEMS][8];
 };
 
@@ -142,7 +150,7 @@ __device__ __forceinline__ void conv_load_row(const ConvTcArgs& a, ConvRegs<CG>&
   const bool rok = gy >= 0 && gy < a.H;
 #pragma unroll
   for (int k = 0; k < ConvRegs<CG>::ITEMS; ++k) {
-    const int idx = tid + k * TC_THREADS;
+    const int idx = tid + k * CONV_THREADS;
     const int cg = idx / PG, q = idx - cg * PG;
     const int gx = x0 - 4 + 4 * q;
     const bool ok = rok && idx < CG * PG && gx >= 0 && gx < a.W;
@@ -159,7 +167,7 @@ __device__ __forceinline__ void conv_store_row(const ConvRegs<CG>& R, uint8_t* d
   constexpr int PG = PW / 4;
 #pragma unroll
   for (int k = 0; k < ConvRegs<CG>::ITEMS; ++k) {
-    const int idx = tid + k * TC_THREADS;
+    const int idx = tid + k * CONV_THREADS;
     if (idx < CG * PG) {
       const int cg = idx / PG, q = idx - cg * PG;
       const float4* v = R.v[k];
@@ -185,7 +193,7 @@ __device__ __forceinline__ void conv_store_row(const ConvRegs<CG>& R, uint8_t* d
 // y + 2 is staged while the MMAs of row y run, so each output row costs one
 // new input row.
 template <int CG, int NP>
-__global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
   using P = ConvTcT<CG, NP>;
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* wsm = sm;
@@ -196,7 +204,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
   // weights -> bfloat16 [tap][cg][n][8], zero beyond Cin / Cout
-  for (int idx = tid; idx < 9 * CG * NP; idx += TC_THREADS) {
+  for (int idx = tid; idx < 9 * CG * NP; idx += CONV_THREADS) {
     const int t = idx / (CG * NP), rem = idx - t * CG * NP, cg = rem / NP, n = rem - cg * NP;
     const int dy = t / 3, dx = t - dy * 3;
     uint32_t pk[4];
@@ -287,15 +295,20 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
       __syncthreads();
       if (s_fail) break;
       tc_fence_after();
-      uint32_t acc[NP];
+      // warp w reads TMEM lanes 32 (w % 4) .. + 31 (= pixels), columns
+      // (w / 4) NP/2 .. + NP/2 - 1 (= output channels)
+      constexpr int HC = NP / 2;
+      const int quarter = warp & 3, n0 = (warp >> 2) * HC;
+      uint32_t acc[HC];
 #pragma unroll
-      for (int q = 0; q < NP / 16; ++q)
-        SHL_TMEM_LD16(acc + 16 * q, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(16 * q));
+      for (int q = 0; q < HC / 8; ++q)
+        SHL_TMEM_LD8(acc + 8 * q, tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(n0 + 8 * q));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x0 + warp * 32 + lane;
+      float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x0 + quarter * 32 + lane;
 #pragma unroll
-      for (int n = 0; n < NP; ++n) {
-        if (n < a.Cout) o[n * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + n) : 0.f);
+      for (int n = 0; n < HC; ++n) {
+        const int ch = n0 + n;
+        if (ch < a.Cout) o[ch * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + ch) : 0.f);
       }
       tc_fence_before();   // TMEM reads done before the next row's MMAs (barrier at loop top)
     }
@@ -648,7 +661,7 @@ cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   int per_sm = (int)((228u * 1024u) / (P::SMEM + 1024u + 256u));
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.numRegs > 0)
-    per_sm = std::min(per_sm, 65536 / (fa.numRegs * TC_THREADS));
+    per_sm = std::min(per_sm, 65536 / (fa.numRegs * CONV_THREADS));
   per_sm = std::max(1, std::min({per_sm, 8, (int)(512 / P::NCOLS)}));
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -663,7 +676,7 @@ cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   args.rows_per_unit = std::min(args.rows_per_unit, a.H);
   const long long nunits = strips * ((a.H + args.rows_per_unit - 1) / args.rows_per_unit);
   const int grid = (int)std::max(1LL, std::min(nunits, (long long)slots));
-  k<<<grid, TC_THREADS, P::SMEM, st>>>(args);
+  k<<<grid, CONV_THREADS, P::SMEM, st>>>(args);
   return cudaGetLastError();
 }
 
