@@ -33,6 +33,23 @@ def _random_bank(K, N, M, rng=RNG):
 
 
 # ------------------------------------------------------------- Sec. 3.3
+def test_shift_lists_golden_file():
+    """tests/golden/shift_indices.txt: the gather lists of Sec. 3.3's shift
+    definitions written out by hand for n = 1..8."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "shift_indices.txt")
+    rows = [l for l in open(path) if l.strip() and not l.startswith("#")]
+    assert len(rows) == 8
+    for line in rows:
+        n, fwd, inv = (part.split() for part in line.split("|"))
+        n = int(n[0])
+        assert list(T.tfftshift_indices(n)) == [int(v) for v in fwd]
+        assert list(T.itfftshift_indices(n)) == [int(v) for v in inv]
+        a = np.arange(n)
+        assert list(np.fft.fftshift(a)) == [int(v) for v in fwd]     # the library routine agrees
+        assert list(np.fft.ifftshift(a)) == [int(v) for v in inv]
+
+
 def test_shift_lists_printed_example():
     # Sec. 3.3: p2 = (n+1)//2 for tfftshift, n - (n+1)//2 for itfftshift.
     assert list(T.tfftshift_indices(5)) == [3, 4, 0, 1, 2]
