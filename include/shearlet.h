@@ -20,7 +20,13 @@
  * default stream).  Every launch goes on that stream; no call synchronises.
  *
  * Images: ``rows`` x ``cols`` real float32, row-major, batch-major:
- * x[b][y][x].  rows and cols are powers of two in [16, 2048].
+ * x[b][y][x].  rows and cols are powers of two in [16, 2048].  Image
+ * arguments (x, x_out, f_masked, f_est, mask) may be device memory of the
+ * bank's device, managed memory, or pinned host memory mapped into the
+ * device's address space (cudaHostAlloc / cudaHostRegister): the first or
+ * last kernel of the call then reads or writes the images over the CPU-GPU
+ * link, with no separate copy.  Other pointers must be device memory.  A
+ * pointer the device cannot dereference gives SHL_EINVAL before any launch.
  *
  * Coefficients: c[b][i][y][x] (batch, filter, row, column), float32 or
  * bfloat16 (round-to-nearest-even on store).  This is the paper's

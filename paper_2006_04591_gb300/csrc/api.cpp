@@ -61,6 +61,25 @@ struct DevGuard {
 
 size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
 
+// Images may live in device memory of the bank's device, in managed memory,
+// or in pinned host memory mapped into the device's address space (the
+// kernels then read or write it over the CPU-GPU link, which moves the
+// image transfer into the first and last kernels).  Returns the address a
+// kernel uses, or nullptr if `device` cannot dereference p.
+template <typename T>
+T* device_view(T* p, int device) {
+  if (!p) return nullptr;
+  cudaPointerAttributes at{};
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type == cudaMemoryTypeDevice) return at.device == device ? p : nullptr;
+  if (at.type == cudaMemoryTypeManaged) return p;
+  if (at.type == cudaMemoryTypeHost && at.devicePointer) return static_cast<T*>(at.devicePointer);
+  return nullptr;
+}
+
 // ------------------------------------------------------- launch accounting
 std::atomic<long long> g_launches{0};
 std::atomic<int> g_profile{0};
@@ -245,6 +264,13 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
     return fail(SHL_EINVAL, "x and coeffs must be 16-byte aligned device pointers");
   if (mode == shl::IN_MASKED && (!mask || !fest || !aligned16(fest) || !aligned16(mask)))
     return fail(SHL_EINVAL, "mask and f_est must be 16-byte aligned device pointers");
+  x = device_view(x, b->device);
+  if (mode == shl::IN_MASKED) {
+    mask = device_view(mask, b->device);
+    fest = device_view(fest, b->device);
+    if (!mask || !fest) return fail(SHL_EINVAL, "mask / f_est not accessible from the bank's device");
+  }
+  if (!x) return fail(SHL_EINVAL, "x not accessible from the bank's device (device or mapped pinned memory)");
   if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
   if (flags & ~SHL_DUAL_WEIGHTED) return fail(SHL_EINVAL, "unknown flags");
   DevGuard g(b->device);
@@ -318,6 +344,8 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
   if (s != SHL_OK || batch == 0) return s;
   if (!coeffs || !x_out || !aligned16(coeffs) || !aligned16(x_out))
     return fail(SHL_EINVAL, "coeffs and x_out must be 16-byte aligned device pointers");
+  x_out = device_view(x_out, b->device);
+  if (!x_out) return fail(SHL_EINVAL, "x_out not accessible from the bank's device (device or mapped pinned memory)");
   if (thresh && (reinterpret_cast<uintptr_t>(thresh) & 3u))
     return fail(SHL_EINVAL, "thresh must be 4-byte aligned");
   if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
@@ -368,6 +396,14 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
   if (reinterpret_cast<uintptr_t>(thresh) & 3u) return fail(SHL_EINVAL, "thresh must be 4-byte aligned");
   if (mask && (!fest || !aligned16(fest) || !aligned16(mask)))
     return fail(SHL_EINVAL, "mask and f_est must be 16-byte aligned device pointers");
+  x = device_view(x, b->device);
+  x_out = device_view(x_out, b->device);
+  if (mask) {
+    mask = device_view(mask, b->device);
+    fest = device_view(fest, b->device);
+    if (!mask || !fest) return fail(SHL_EINVAL, "mask / f_est not accessible from the bank's device");
+  }
+  if (!x || !x_out) return fail(SHL_EINVAL, "x / x_out not accessible from the bank's device");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;

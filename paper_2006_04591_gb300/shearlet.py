@@ -189,37 +189,37 @@ def shl_workspace_size(h, op, batch):
 def shl_decompose(h, x, batch, coeffs, dtype, flags, ws, stream=None):
     _check("shl_decompose", lib().shl_decompose(
         h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _ptr(ws), ws.numel() * ws.element_size(),
-        _stream(stream, x.device)))
+        _stream(stream, coeffs.device)))
 
 
 def shl_decompose_noalloc(h, x, batch, coeffs, dtype, flags, stream=None):
     """shl_decompose using the library's fixed scratch instead of a workspace."""
     _check("shl_decompose_noalloc", lib().shl_decompose_noalloc(
-        h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _stream(stream, x.device)))
+        h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _stream(stream, coeffs.device)))
 
 
 def shl_decompose_masked(h, f_masked, mask, f_est, batch, coeffs, dtype, ws, stream=None):
     _check("shl_decompose_masked", lib().shl_decompose_masked(
         h, _ptr(f_masked), _ptr(mask), _ptr(f_est), batch, _ptr(coeffs), dtype, _ptr(ws),
-        ws.numel() * ws.element_size(), _stream(stream, f_masked.device)))
+        ws.numel() * ws.element_size(), _stream(stream, coeffs.device)))
 
 
 def shl_reconstruct(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
     _check("shl_reconstruct", lib().shl_reconstruct(
         h, _ptr(coeffs), dtype, batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
-        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+        ws.numel() * ws.element_size(), _stream(stream, coeffs.device)))
 
 
 def shl_shrink(h, x, mask, f_est, batch, thresh, x_out, ws, stream=None):
     _check("shl_shrink", lib().shl_shrink(
         h, _ptr(x), _ptr(mask), _ptr(f_est), batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
-        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+        ws.numel() * ws.element_size(), _stream(stream, ws.device)))
 
 
 def shl_adjoint(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
     _check("shl_adjoint", lib().shl_adjoint(
         h, _ptr(coeffs), dtype, batch, _ptr(thresh), _ptr(x_out), _ptr(ws),
-        ws.numel() * ws.element_size(), _stream(stream, x_out.device)))
+        ws.numel() * ws.element_size(), _stream(stream, coeffs.device)))
 
 
 def shl_subband_absmax(h, coeffs, dtype, batch, by_rms, out, stream=None):
@@ -299,11 +299,17 @@ class Bank:
         return torch.empty(max(n, 16), dtype=torch.uint8, device="cuda:%d" % self.device)
 
     def _check_images(self, x):
+        """Images are CUDA tensors, or pinned host tensors that the kernels read
+        / write over the CPU-GPU link (the C ABI maps them)."""
         if x.dim() != 3 or x.shape[1:] != (self.rows, self.cols):
             raise ValueError("expected [B, %d, %d] images, got %s" % (self.rows, self.cols,
                                                                      tuple(x.shape)))
-        if not x.is_cuda or not x.is_contiguous():
-            raise ValueError("images must be contiguous CUDA tensors")
+        if not x.is_contiguous() or not (x.is_cuda or x.is_pinned()):
+            raise ValueError("images must be contiguous CUDA or pinned host tensors")
+
+    def _dev(self):
+        import torch
+        return torch.device("cuda", self.device)
 
     def decompose(self, x, dtype=None, dual=False, out=None, ws=None):
         import torch
@@ -312,7 +318,7 @@ class Bank:
         self._check_images(x)
         B = x.shape[0]
         c = out if out is not None else torch.empty((B, self.K, self.rows, self.cols),
-                                                    dtype=dtype, device=x.device)
+                                                    dtype=dtype, device=self._dev())
         ws = ws if ws is not None else self.workspace(SHL_OP_DECOMPOSE, B)
         shl_decompose(self.handle, x, B, c, _dtype_code(c.dtype),
                       SHL_DUAL_WEIGHTED if dual else 0, ws)
@@ -324,7 +330,7 @@ class Bank:
         self._check_images(f_masked)
         B = f_masked.shape[0]
         c = out if out is not None else torch.empty((B, self.K, self.rows, self.cols),
-                                                    dtype=dtype, device=f_masked.device)
+                                                    dtype=dtype, device=self._dev())
         ws = ws if ws is not None else self.workspace(SHL_OP_DECOMPOSE, B)
         shl_decompose_masked(self.handle, f_masked, mask_u8, f_est, B, c,
                              _dtype_code(c.dtype), ws)
@@ -359,7 +365,7 @@ class Bank:
         x = x.contiguous()
         self._check_images(x)
         B = x.shape[0]
-        thresh = thresh.to(device=x.device, dtype=torch.float32).contiguous()
+        thresh = thresh.to(device=self._dev(), dtype=torch.float32).contiguous()
         if thresh.shape != (B, self.K):
             raise ValueError("thresholds must be [B, K]")
         if (mask_u8 is None) != (f_est is None):
@@ -368,7 +374,8 @@ class Bank:
             mask_u8 = mask_u8.contiguous()
             f_est = f_est.contiguous()
             self._check_images(f_est)
-        y = out if out is not None else torch.empty_like(x)
+        y = out if out is not None else torch.empty(x.shape, dtype=torch.float32,
+                                                    device=self._dev())
         ws = ws if ws is not None else self.workspace(SHL_OP_SHRINK, B)
         shl_shrink(self.handle, x, mask_u8, f_est, B, thresh, y, ws)
         return y

@@ -251,3 +251,36 @@ def test_chunking_does_not_change_results():
     b = torch.empty_like(a)
     S.shl_decompose_noalloc(bank.handle, x, 4, b, S.SHL_F32, 0)
     assert torch.equal(a, b)
+
+
+# ------------------------------------------- images in mapped pinned memory
+def test_pinned_host_images_give_the_same_bits():
+    """Images in pinned host memory are read / written by the first / last
+    kernel over the CPU-GPU link: the same bits as with device images."""
+    ref, bank = _bank(256, 256, 3)
+    x = _images(3, 256, 256, 97)
+    xd = torch.from_numpy(x).cuda()
+    xh = torch.from_numpy(x).pin_memory()
+    c_dev = bank.decompose(xd)
+    c_host = bank.decompose(xh)
+    torch.cuda.synchronize()
+    assert torch.equal(c_dev, c_host)
+    yh = torch.empty((3, 256, 256), dtype=torch.float32).pin_memory()
+    bank.reconstruct(c_dev, out=yh)
+    torch.cuda.synchronize()
+    assert torch.equal(bank.reconstruct(c_dev).cpu(), yh)
+    th = torch.full((3, bank.K), 0.05)
+    sh = torch.empty((3, 256, 256), dtype=torch.float32).pin_memory()
+    bank.shrink(xh, th, out=sh)
+    torch.cuda.synchronize()
+    assert torch.equal(bank.shrink(xd, th).cpu(), sh)
+
+
+def test_unmapped_host_memory_is_rejected():
+    from paper_2006_04591_gb300 import shearlet as S
+    ref, bank = _bank(32, 32, 2)
+    x = torch.zeros((1, 32, 32))                       # pageable, not registered
+    c = torch.empty((1, bank.K, 32, 32), device="cuda")
+    ws = bank.workspace(S.SHL_OP_DECOMPOSE, 1)
+    with pytest.raises(S.ShearletError):
+        S.shl_decompose(bank.handle, x, 1, c, S.SHL_F32, 0, ws)
