@@ -284,3 +284,47 @@ def test_unmapped_host_memory_is_rejected():
     ws = bank.workspace(S.SHL_OP_DECOMPOSE, 1)
     with pytest.raises(S.ShearletError):
         S.shl_decompose(bank.handle, x, 1, c, S.SHL_F32, 0, ws)
+
+
+# ----------------------------------------------------- sizes and degenerate banks
+def test_max_size_2048():
+    """2048 x 2048 (the largest size the library takes), 2 scales: sampled
+    subbands against the oracle, perfect reconstruction, adjoint identity."""
+    ref, bank = _bank(2048, 2048, 2)
+    x = _images(1, 2048, 2048, 123)
+    xt = torch.from_numpy(x).cuda()
+    c = bank.decompose(xt)
+    for i in (0, 5, 16):
+        want = OT.decompose(x[0], ref["psi_hat"][i:i + 1]).real[0]
+        assert _rel(c[0, i].cpu().numpy(), want) <= TOL32, i
+    r = bank.reconstruct(c)
+    assert (r - xt).abs().max().item() <= TOL32 * xt.abs().max().item()
+    w = torch.randn(c.shape, generator=torch.Generator().manual_seed(3)).cuda()
+    a = bank.adjoint(w)
+    lhs = (c.double() * w.double()).sum().item()
+    rhs = (xt.double() * a.double()).sum().item()
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_identity_bank_is_identity():
+    """One filter G = 1 (W = 1): decomposition and reconstruction return the image."""
+    from paper_2006_04591_gb300.shearlet import Bank
+    bank = Bank.from_spectra(np.ones((1, 64, 128)), device=0)
+    x = torch.from_numpy(_images(2, 64, 128, 7)).cuda()
+    c = bank.decompose(x)
+    assert c.shape == (2, 1, 64, 128)
+    assert (c[:, 0] - x).abs().max().item() <= 1e-6 * x.abs().max().item()
+    assert (bank.reconstruct(c) - x).abs().max().item() <= 1e-6 * x.abs().max().item()
+    assert (bank.adjoint(c) - x).abs().max().item() <= 1e-6 * x.abs().max().item()
+
+
+def test_single_scale_bank():
+    """J = 1 (one scale, shear level 1): parity and perfect reconstruction."""
+    ref, bank = _bank(128, 64, 1)
+    x = _images(2, 128, 64, 11)
+    c = bank.decompose(torch.from_numpy(x).cuda()).cpu().numpy()
+    want, _ = OT.decompose_batch(x, ref["psi_hat"])
+    for b in range(2):
+        assert _rel(c[b], want[b]) <= TOL32
+    r = bank.reconstruct(torch.from_numpy(c).cuda()).cpu().numpy()
+    assert np.abs(r - x).max() <= TOL32 * np.abs(x).max()
