@@ -132,3 +132,40 @@ def test_coeff_net_tc_matches_rounded_reference():
     l2 = lambda a, b: ((a.detach().double().cpu() - b).norm() / b.norm()).item()
     assert l2(y, yo) <= 1e-4
     assert l2(net.w0.grad, w0.grad) <= 1e-3
+
+
+WS_CHILD = """
+import torch
+from oracle import nn as ON
+from paper_2006_04591_gb300 import nn
+def bf(t): return t.to(torch.bfloat16).double()
+for (B, Ci, Co, H, W) in [(2, 33, 32, 5, 128), (1, 32, 48, 9, 256), (1, 2, 16, 3, 128)]:
+    g = torch.Generator().manual_seed(B * 7 + Ci + H)
+    x = torch.randn((B, Ci, H, W), generator=g)
+    w = torch.randn((Co, Ci, 3, 3), generator=g) * 0.2
+    b = torch.randn(Co, generator=g)
+    out = torch.empty((B, Co, H, W), device="cuda")
+    nn.shl_nn_conv3x3_forward_tc(x.cuda(), w.cuda(), b.cuda(), out)
+    nn.shl_nn_tc_status()
+    want = ON.conv3x3(bf(x), bf(w), b.double())
+    err = ((out.double().cpu() - want).abs().max() / want.abs().max()).item()
+    assert err <= 2e-5, (B, Ci, Co, H, W, err)
+print("ws ok")
+"""
+
+
+def test_warp_specialised_conv_matches_rounded_oracle():
+    """The opt-in warp-specialised forward kernel (SHL_CONV_WS=1), in a child
+    process: producers, MMA issuer and epilogue handing rows over through
+    mbarriers give the rounded oracle's result."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    env = dict(os.environ)
+    env["PYTHONPATH"] = root + os.pathsep + env.get("PYTHONPATH", "")
+    env["SHL_CONV_WS"] = "1"
+    r = subprocess.run([sys.executable, "-c", WS_CHILD], cwd=root, env=env, capture_output=True,
+                       text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "ws ok" in r.stdout
