@@ -14,13 +14,18 @@
 //   k_dec_lines   Z = IFFT_y(G_i * scale [* 1/W] * X_b) per subband line
 //                 (the filter multiply of Sec. 3.4 fused into the load).
 //   k_rec_lines   one CTA per (image, kx): lane groups split the chunk's
-//                 filters, FFT_y each staged line, multiply by G_i, sum in
-//                 registers; the CTA adds the partial sums in fixed order,
-//                 and on the image's last chunk applies scale [* 1/W] and the
-//                 inverse column FFT (Sec. 3.4 reconstruction).
+//                 filters, FFT_y each staged line (the next one prefetched
+//                 with cp.async), multiply by G_i, sum in registers; the CTA
+//                 adds the partial sums in fixed order, and on the image's
+//                 last chunk applies scale [* 1/W] and the inverse column
+//                 FFT (Sec. 3.4 reconstruction).
+//   k_rows_shrink_t  in place on staged half spectra: C2R rows -> hard
+//                 threshold in registers -> R2C rows (fused denoise / IHT).
+//   k_dec_pipe    opt-in: k_dec_lines + k_rows_c2r_t in one cooperative
+//                 launch over an L2-resident staging ring.
 //
 // Real-row packing: z[n] = x[2n] + i x[2n+1] with a length-M/2 complex FFT
-// and the conjugate-pair split (see rows.cu of the reference derivation):
+// and the conjugate-pair split (the standard real-FFT identities):
 //   R2C: X[k] = E[k] + exp(-2 pi i k/M) O[k], E = (Z[k] + conj Z[L-k]) / 2,
 //        O = -i (Z[k] - conj Z[L-k]) / 2, X[L] = Re Z[0] - Im Z[0];
 //   C2R: Z[k] = (X[k] + conj X[L-k]) + i exp(+2 pi i k/M) (X[k] - conj X[L-k]),
