@@ -24,8 +24,6 @@ from __future__ import annotations
 import argparse
 import json
 import math
-import queue
-import threading
 import time
 
 import numpy as np
@@ -75,55 +73,53 @@ def make_net(bank: Bank, T=10, delta0=5.0, delta_min=0.02, seed=0, pool=4, ch=32
     return net
 
 
+def _make_pairs(args):
+    """One training batch: cartoon+texture images and Bernoulli masks (uint8)
+    for the given seeds (runs in a worker process)."""
+    n, p, seeds = args
+    clean = np.stack([synth.cartoon_texture(n, n, int(s)) for s in seeds]).astype(np.float32)
+    mask = np.stack([synth.bernoulli_mask(n, n, p, 50_000 + int(s)) for s in seeds])
+    return clean, mask.astype(np.uint8)
+
+
 class _Pairs:
-    """Seeded (clean, mask) batches produced ahead by worker threads.
+    """Seeded (clean, mask) batches produced ahead by a pool of spawned worker
+    processes (the numpy image synthesis would otherwise bound the training
+    step on the host).
 
     The seeds of every step are drawn up front, so the training data order is
-    deterministic; workers fill steps in a bounded window ahead of the
-    consumer."""
+    deterministic; at most `depth` batches are in flight or waiting."""
 
-    def __init__(self, n, seed0, n_pairs, batch, steps, p=0.5, rng_seed=0, workers=6, depth=12):
+    def __init__(self, n, seed0, n_pairs, batch, steps, p=0.5, rng_seed=0, workers=None, depth=None):
+        import multiprocessing as mp
+        import os
+        from collections import deque
         rng = np.random.default_rng(rng_seed)
         self.seeds = seed0 + rng.integers(0, n_pairs, size=(steps, batch))
         self.n, self.p = n, p
-        self.ready = {}
-        self.next_get = 0
-        self.cv = threading.Condition()
-        self.stop = False
-        self.depth = depth
-        self.threads = [threading.Thread(target=self._work, args=(w, workers), daemon=True)
-                        for w in range(workers)]
-        for t in self.threads:
-            t.start()
+        nw = workers or max(1, min(16, (os.cpu_count() or 2) - 1))
+        self.pool = mp.get_context("spawn").Pool(nw)
+        self.pending = deque()
+        self.next_submit = 0
+        self.depth = depth or 2 * nw
+        while self.next_submit < min(self.depth, len(self.seeds)):
+            self._submit()
 
-    def _work(self, w, nw):
-        for k in range(w, len(self.seeds), nw):
-            with self.cv:
-                while not self.stop and k >= self.next_get + self.depth:
-                    self.cv.wait(timeout=1.0)
-                if self.stop:
-                    return
-            seeds = self.seeds[k]
-            clean = np.stack([synth.cartoon_texture(self.n, self.n, int(s)) for s in seeds])
-            mask = np.stack([synth.bernoulli_mask(self.n, self.n, self.p, 50_000 + int(s))
-                             for s in seeds])
-            with self.cv:
-                self.ready[k] = (clean.astype(np.float32), mask.astype(np.float32))
-                self.cv.notify_all()
+    def _submit(self):
+        args = (self.n, self.p, self.seeds[self.next_submit])
+        self.pending.append(self.pool.apply_async(_make_pairs, (args,)))
+        self.next_submit += 1
 
     def get(self):
-        with self.cv:
-            while self.next_get not in self.ready:
-                self.cv.wait(timeout=1.0)
-            item = self.ready.pop(self.next_get)
-            self.next_get += 1
-            self.cv.notify_all()
-        return item
+        res = self.pending.popleft()
+        if self.next_submit < len(self.seeds):
+            self._submit()
+        clean, mask = res.get(timeout=600)
+        return clean, mask.astype(np.float32)
 
     def close(self):
-        with self.cv:
-            self.stop = True
-            self.cv.notify_all()
+        self.pool.terminate()
+        self.pool.join()
 
 
 def train_thresholds(bank: Bank, steps=300, batch=4, T=10, n_pairs=2000, seed0=10000, lr=2e-3,
@@ -274,7 +270,7 @@ def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3, tc=True):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--size", type=int, default=512)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--out", default=None)
     ap.add_argument("--coeff-net", action="store_true", help="time the coefficient-network step")
