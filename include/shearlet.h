@@ -20,7 +20,11 @@
  * default stream).  Every launch goes on that stream; no call synchronises.
  *
  * Images: ``rows`` x ``cols`` real float32, row-major, batch-major:
- * x[b][y][x].  rows and cols are powers of two in [16, 2048].  Image
+ * x[b][y][x].  rows and cols are in [1, 4096].  Powers of two in
+ * [16, 2048] with real spectra run on the half-spectrum kernels; every other
+ * size, and every bank with complex spectra, runs on the general kernels
+ * (full complex planes, mixed-radix or Bluestein line DFTs; the same results
+ * to float32 rounding, at a lower throughput).  Image
  * arguments (x, x_out, f_masked, f_est, mask) may be device memory of the
  * bank's device, managed memory, or pinned host memory mapped into the
  * device's address space (cudaHostAlloc / cudaHostRegister): the first or
@@ -34,9 +38,13 @@
  * axes (paper coeffs[0, y, x, i] == c[0][i][y][x]), so each subband is one
  * contiguous image.
  *
- * Filters: K real, even spectra G_i in natural DFT order (index 0 = zero
- * frequency), i.e. ifftshift of the paper's centred ``shearletFilters[i]``.
- * The library keeps the half-spectrum columns 0..cols/2 on the device.
+ * Filters: K spectra G_i in natural DFT order (index 0 = zero frequency),
+ * i.e. ifftshift of the conjugated centred ``shearletFilters[i]`` of the
+ * paper.  Decomposition multiplies the image spectrum by G_i, reconstruction
+ * by conj(G_i) / W with W = sum_i |G_i|^2 (Sec. 3.4).  Real spectra must be
+ * even, complex ones Hermitian, G(-k) = conj(G(k)), so that real images have
+ * real coefficients.  The shift pairs of the paper cancel at every size:
+ * a circular translation commutes with the filtering.
  *
  * Ownership: the library owns a bank (device spectra, 1/W, RMS, indices).
  * The caller owns all image, coefficient, threshold and workspace buffers,
@@ -100,9 +108,12 @@ const char* shl_last_error_detail(void);
  * mirror g, iterated filters h_j / g_j, McClellan fan filter P, digital
  * shear of Eqs. 2.4-2.5.  Order: 0 = low-pass, then per scale (coarse to
  * fine) cone 1 with shear k ascending, then cone 2 with k ascending.
+ * rows, cols in [1, 4096] (the float64 line DFTs of the construction use
+ * Bluestein's algorithm at lengths that are not powers of two).
  * device < 0 builds a host-only bank: shl_bank_query / shl_bank_copy_info
  * work (no GPU needed), transform calls return SHL_EINVAL.
- * Errors: SHL_EINVAL for bad sizes / levels, SHL_ENOMEM, SHL_ECUDA.
+ * Errors: SHL_EUNSUPPORTED for sizes outside [1, 4096], SHL_EINVAL for bad
+ * levels, SHL_ENOMEM, SHL_ECUDA.
  */
 shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_levels,
                            int full, int device, shl_bank** out);
@@ -115,7 +126,8 @@ shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_le
  * result is the bank shl_bank_create builds, to float64 rounding (the host
  * copies read by shl_bank_copy_info are downloaded).  The paper times this
  * construction as its first experiment (filters on the GPU vs the CPU).
- * device >= 0; errors as shl_bank_create.
+ * rows and cols powers of two in [16, 2048] (else SHL_EUNSUPPORTED; build
+ * other sizes with shl_bank_create); device >= 0; errors as shl_bank_create.
  */
 shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shear_levels,
                                int full, int device, shl_bank** out);
@@ -128,11 +140,30 @@ shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shea
  *            weights W = sum_i G_i^2 must be > 0 everywhere, else SHL_EINVAL.
  *   idx      host int [K][3] (cone, scale, shear) copied for reference, or
  *            NULL (all zeros).
+ * rows, cols in [1, 4096] (SHL_EUNSUPPORTED otherwise).
  * RMS_i = sqrt(sum G_i^2 / (rows cols)) is computed in float64.
  * device < 0 builds a host-only bank as for shl_bank_create.
  */
 shl_status shl_bank_create_from_spectra(int rows, int cols, int K, const double* spectra,
                                         const int* idx, int device, shl_bank** out);
+
+/*
+ * shl_bank_create_general - a bank that always runs on the general kernels,
+ * with real or complex spectra (Sec. 3.4 allows complex filter tensors; the
+ * paper's listings keep complex64 spectra).
+ *   spectra_re, spectra_im  host float64 [K][rows][cols], natural order;
+ *            spectra_im NULL for real spectra.  Complex spectra must be
+ *            Hermitian, G(-k) == conj(G(k)), real ones even, to 1e-9 of the
+ *            largest |G|; W = sum_i |G_i|^2 > 0 everywhere; else SHL_EINVAL.
+ *   idx      as for shl_bank_create_from_spectra.
+ * rows, cols in [1, 4096].  The decomposition computes
+ * c_i = IDFT2(G_i DFT2 x) (real by Hermitian symmetry), the reconstruction
+ * IDFT2(sum_i conj(G_i) DFT2 c_i / W), the adjoints as for real banks.
+ * device < 0 builds a host-only bank.
+ */
+shl_status shl_bank_create_general(int rows, int cols, int K, const double* spectra_re,
+                                   const double* spectra_im, const int* idx, int device,
+                                   shl_bank** out);
 
 shl_status shl_bank_destroy(shl_bank* bank);
 
@@ -143,21 +174,31 @@ shl_status shl_bank_query(const shl_bank* bank, int* K, int* rows, int* cols);
  * shl_bank_copy_info - copy host-side float64 data of a bank (Sec. 3.4: the
  * system's filters, its RMS array and its index array; and the dual frame
  * weights ``tfdualFrameWeights``).  Any out pointer may be NULL.
- *   idx [K][3], rms [K], spectra [K][rows][cols] natural order,
- *   dual_w [rows][cols] natural order (W = sum_i G_i^2).
+ *   idx [K][3], rms [K], spectra [K][rows][cols] natural order (the real
+ *   parts for a complex bank), dual_w [rows][cols] natural order
+ *   (W = sum_i |G_i|^2).
  */
 shl_status shl_bank_copy_info(const shl_bank* bank, int* idx, double* rms, double* spectra,
                               double* dual_w);
+
+/* Imaginary parts [K][rows][cols] of the spectra (zeros for a real bank). */
+shl_status shl_bank_copy_spectra_imag(const shl_bank* bank, double* imag);
+
+/* *general = 1 when the bank runs on the general kernels, 0 on the
+ * power-of-two half-spectrum kernels. */
+shl_status shl_bank_path(const shl_bank* bank, int* general);
 
 /*
  * shl_workspace_size - bytes of device workspace ``op`` needs for ``batch``
  * images.  The workspace holds the image spectra (decompose) or the
  * per-image accumulators (reconstruct / adjoint) plus a staging area for
- * per-subband intermediates.  Decomposition at rows, cols in {512, 1024}
- * runs pipelined and stages 24 subband planes (25 MB at 512 x 512) plus a
- * few counters per 8 subbands; other sizes, and the reconstruction, stage
- * up to 1 GiB (e.g. all 784 subbands of 16 images at 512 x 512 with 49
- * filters).  Its contents on entry are ignored.
+ * per-subband intermediates: up to 1 GiB of staging (e.g. all 784
+ * subbands of 16 images at 512 x 512 with 49 filters).  A plane is
+ * rows * (cols/2 + 1) complex float32 on the power-of-two path and
+ * rows * cols complex float32 on the general path.  With the environment
+ * variable SHL_PIPE=1 the power-of-two decomposition at rows = 512, cols in
+ * {512, 1024} runs pipelined and stages 24 planes plus a few counters per 8
+ * subbands instead.  Its contents on entry are ignored.
  */
 shl_status shl_workspace_size(const shl_bank* bank, shl_op op, int batch, size_t* bytes);
 

@@ -27,11 +27,16 @@ Filter spectra ``psi_hat`` are centred (zero frequency at index n//2 after
 Coefficients have shape ``[K, N, M]``; the paper's ``coeffs[0, y, x, i]`` is
 ``c[i, y, x]`` here.
 
-The natural-order functions drop both shifts: for even N and M the two
-``(-1)^(k1+k2)`` modulations that the shifts introduce cancel, so
-``c_i = ifft2(fft2(f) * G_i)`` with ``G_i = ifftshift(conj(psi_hat_i))``.
-They exist so that a test can check that algebra, and so that banks given in
-natural order (the CUDA library's layout) can be fed to the oracle.
+The natural-order functions drop both shifts.  The frequency-side pair
+(``tfftshift`` of the image spectrum, ``itfftshift`` of the product) is a
+permutation applied to both factors and undone, so it moves onto the filter:
+``G_i = itfftshift(conj(psi_hat_i))``.  The space-side pair is a circular
+translation of the image by ``p2`` before the filtering and back after it,
+and circular filtering commutes with translations.  Hence
+``c_i = ifft2(fft2(f) * G_i)`` at every size, odd or even (for even sizes it
+is also the cancellation of the two ``(-1)^(k1+k2)`` modulations).  These
+functions exist so that a test can check that algebra, and so that banks
+given in natural order (the CUDA library's layout) can be fed to the oracle.
 """
 
 from __future__ import annotations
@@ -157,13 +162,13 @@ def centred_to_natural(psi_hat: np.ndarray) -> np.ndarray:
 
 
 def decompose_natural(f: np.ndarray, G: np.ndarray) -> np.ndarray:
-    """c_i = ifft2(fft2(f) * G_i); valid form for even N and M only."""
+    """c_i = ifft2(fft2(f) * G_i), any N and M."""
     X = np.fft.fft2(np.asarray(f, dtype=np.complex128))
     return np.fft.ifft2(X[None] * G, axes=(-2, -1))
 
 
 def reconstruct_natural(c: np.ndarray, G: np.ndarray, weights=True):
-    """ifft2(sum_i conj(G_i) fft2(c_i) [/ W]); even N and M only."""
+    """ifft2(sum_i conj(G_i) fft2(c_i) [/ W]), any N and M."""
     acc = np.sum(np.conj(G) * np.fft.fft2(c, axes=(-2, -1)), axis=0)
     if weights:
         acc = acc / np.sum(np.abs(G) ** 2, axis=0)

@@ -2,7 +2,9 @@
 //
 // Validation, bank ownership and the launch sequences of the transform live
 // here; all arithmetic on images and coefficients runs in the kernels of
-// fast.cu (and nn.cu for the learned parts).
+// fast.cu (power-of-two sizes 16..2048 with real, even spectra), general.cu
+// (every other size, and complex Hermitian spectra) and nn.cu / nn_tc.cu
+// (the learned parts).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -18,6 +20,7 @@
 #include <vector>
 
 #include "../../include/shearlet.h"
+#include "general.h"
 #include "internal.h"
 
 struct shl_bank {
@@ -30,6 +33,14 @@ struct shl_bank {
   float* dInvW = nullptr;        // [Mh][N]
   float2* dTw = nullptr;         // [TW_P]
   float* dRms = nullptr;         // [K]
+  // General path (general.cu): full complex planes in natural order.
+  bool general = false;          // this bank runs on general.cu
+  bool cplx = false;             // complex spectra (imaginary parts kept)
+  std::vector<double> spectra_im;  // [K][N][M] when cplx
+  void* dGg = nullptr;           // float [K][N][M], or float2 [K][N][M] when cplx
+  float* dInvWg = nullptr;       // [N][M]
+  float2* dTab = nullptr;        // line tables of both plans
+  shl::gen::LinePlan planN{}, planM{};
 };
 
 namespace {
@@ -124,7 +135,11 @@ int stage_subbands(const shl_bank* b) {
   return s < 1 ? 1 : s;
 }
 
-size_t plane_bytes(const shl_bank* b) { return (size_t)b->N * b->Mh * sizeof(float2); }
+// Bytes of one spectrum plane: half spectrum on the power-of-two path, full
+// complex plane on the general path.
+size_t plane_bytes(const shl_bank* b) {
+  return (size_t)b->N * (b->general ? b->M : b->Mh) * sizeof(float2);
+}
 
 // Pipelined decomposition: chunk of CS subbands, NS ring slots.  Opt-in
 // (SHL_PIPE=1): it keeps the staging in L2 but measured slower than the
@@ -148,7 +163,9 @@ const PipeCfg& pipe_cfg() {
   }();
   return c;
 }
-bool use_pipe(const shl_bank* b) { return pipe_cfg().on && shl::dec_pipe_supported(b->N, b->M); }
+bool use_pipe(const shl_bank* b) {
+  return !b->general && pipe_cfg().on && shl::dec_pipe_supported(b->N, b->M);
+}
 
 size_t ws_need(const shl_bank* b, int batch, shl_op op) {
   const long long sub = (long long)batch * b->K;
@@ -171,6 +188,9 @@ void free_bank(shl_bank* b) {
   if (b->dInvW) cudaFree(b->dInvW);
   if (b->dTw) cudaFree(b->dTw);
   if (b->dRms) cudaFree(b->dRms);
+  if (b->dGg) cudaFree(b->dGg);
+  if (b->dInvWg) cudaFree(b->dInvWg);
+  if (b->dTab) cudaFree(b->dTab);
   delete b;
 }
 
@@ -185,6 +205,52 @@ std::vector<float2> twiddle_table() {
   return hT;
 }
 
+// Tables of the general path: float32 filters (complex when the bank keeps
+// imaginary parts), 1/W, and the line plans of both axes.
+shl_status upload_general(shl_bank* b) {
+  const int N = b->N, M = b->M, K = b->K;
+  const size_t plane = (size_t)N * M;
+  std::vector<float> hW(plane), hR(K);
+  for (size_t e = 0; e < plane; ++e) hW[e] = (float)(1.0 / b->dual_w[e]);
+  for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
+  std::vector<float> hG;
+  std::vector<float2> hGc;
+  if (b->cplx) {
+    hGc.resize((size_t)K * plane);
+    for (size_t e = 0; e < hGc.size(); ++e)
+      hGc[e] = make_float2((float)b->spectra[e], (float)b->spectra_im[e]);
+  } else {
+    hG.resize((size_t)K * plane);
+    for (size_t e = 0; e < hG.size(); ++e) hG[e] = (float)b->spectra[e];
+  }
+  shl::gen::LineTables tN = shl::gen::make_line_tables(N), tM = shl::gen::make_line_tables(M);
+  const size_t gbytes = b->cplx ? hGc.size() * sizeof(float2) : hG.size() * sizeof(float);
+  const size_t tabs = tN.data.size() + tM.data.size();
+  DevGuard g(b->device);
+  if (cudaMalloc(&b->dGg, gbytes) != cudaSuccess ||
+      cudaMalloc(&b->dInvWg, plane * sizeof(float)) != cudaSuccess ||
+      cudaMalloc(&b->dTab, tabs * sizeof(float2)) != cudaSuccess ||
+      cudaMalloc(&b->dRms, K * sizeof(float)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(SHL_ENOMEM, "cudaMalloc failed for the filter bank");
+  }
+  cudaError_t e;
+  const void* gsrc = b->cplx ? (const void*)hGc.data() : (const void*)hG.data();
+  if ((e = cudaMemcpy(b->dGg, gsrc, gbytes, cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dInvWg, hW.data(), plane * sizeof(float), cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dTab, tN.data.data(), tN.data.size() * sizeof(float2),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dTab + tN.data.size(), tM.data.data(), tM.data.size() * sizeof(float2),
+                      cudaMemcpyHostToDevice)) ||
+      (e = cudaMemcpy(b->dRms, hR.data(), K * sizeof(float), cudaMemcpyHostToDevice)))
+    return cuda_fail(e, "bank upload");
+  shl::gen::place_line_tables(&tN, b->dTab);
+  shl::gen::place_line_tables(&tM, b->dTab + tN.data.size());
+  b->planN = tN.plan;
+  b->planM = tM.plan;
+  return SHL_OK;
+}
+
 shl_status upload_bank(shl_bank* b) {
   const int N = b->N, M = b->M, Mh = b->Mh, K = b->K;
   const bool host_only = b->device < 0;
@@ -192,16 +258,19 @@ shl_status upload_bank(shl_bank* b) {
   b->rms.assign(K, 0.0);
   for (int i = 0; i < K; ++i) {
     const double* G = b->spectra.data() + (size_t)i * N * M;
+    const double* Gi = b->cplx ? b->spectra_im.data() + (size_t)i * N * M : nullptr;
     double s = 0.0;
     for (size_t e = 0; e < (size_t)N * M; ++e) {
-      b->dual_w[e] += G[e] * G[e];
-      s += G[e] * G[e];
+      const double m2 = G[e] * G[e] + (Gi ? Gi[e] * Gi[e] : 0.0);   // |G_i|^2
+      b->dual_w[e] += m2;
+      s += m2;
     }
     b->rms[i] = std::sqrt(s / (double(N) * M));
   }
   for (size_t e = 0; e < (size_t)N * M; ++e)
-    if (!(b->dual_w[e] > 0.0)) return fail(SHL_EINVAL, "dual frame weights W = sum G_i^2 must be > 0");
+    if (!(b->dual_w[e] > 0.0)) return fail(SHL_EINVAL, "dual frame weights W = sum |G_i|^2 must be > 0");
   if (host_only) return SHL_OK;
+  if (b->general) return upload_general(b);
   std::vector<float> hG((size_t)K * N * Mh), hW((size_t)N * Mh), hR(K);
   for (int i = 0; i < K; ++i)
     for (int y = 0; y < N; ++y)
@@ -228,9 +297,18 @@ shl_status upload_bank(shl_bank* b) {
   return SHL_OK;
 }
 
+// Power-of-two sizes the kernels of fast.cu cover.
+bool fast_size(int rows, int cols) { return pow2_in(rows, 16, 2048) && pow2_in(cols, 16, 2048); }
+
 shl_status check_size(int rows, int cols) {
-  if (!pow2_in(rows, 16, 2048) || !pow2_in(cols, 16, 2048))
+  if (!fast_size(rows, cols))
     return fail(SHL_EUNSUPPORTED, "rows and cols must be powers of two in [16, 2048]");
+  return SHL_OK;
+}
+
+shl_status check_general_size(int rows, int cols) {
+  if (rows < 1 || cols < 1 || rows > shl::gen::MAX_LEN || cols > shl::gen::MAX_LEN)
+    return fail(SHL_EUNSUPPORTED, "rows and cols must be in [1, 4096]");
   return SHL_OK;
 }
 
@@ -245,6 +323,16 @@ shl_status check_common(const shl_bank* b, int batch, const void* ws, size_t ws_
     return fail(SHL_EINVAL, "workspace too small (see shl_workspace_size)");
   return SHL_OK;
 }
+
+cudaError_t gen_decompose(const shl_bank* b, shl::InMode mode, const float* x,
+                          const unsigned char* mask, const float* fest, int batch, void* coeffs,
+                          shl_dtype dtype, bool dual, void* ws, int S, cudaStream_t st);
+cudaError_t gen_reconstruct(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                            const float* thresh, float* x_out, void* ws, bool weights,
+                            cudaStream_t st);
+cudaError_t gen_shrink(const shl_bank* b, const float* x, const unsigned char* mask,
+                       const float* fest, int batch, const float* thresh, float* x_out, void* ws,
+                       cudaStream_t st);
 
 shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
                           const unsigned char* mask, const float* fest, int batch, void* coeffs,
@@ -275,6 +363,12 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   if (flags & ~SHL_DUAL_WEIGHTED) return fail(SHL_EINVAL, "unknown flags");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->general) {
+    const int S = stage_override > 0 ? stage_override : stage_subbands(b);
+    cudaError_t e = gen_decompose(b, mode, x, mask, fest, batch, coeffs, dtype,
+                                  (flags & SHL_DUAL_WEIGHTED) != 0, ws, S, st);
+    return e ? cuda_fail(e, "general decomposition") : SHL_OK;
+  }
   const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
   float2* X = static_cast<float2*>(ws);
   float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
@@ -351,6 +445,10 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
   if (dtype != SHL_F32 && dtype != SHL_BF16) return fail(SHL_EINVAL, "bad dtype");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->general) {
+    cudaError_t e = gen_reconstruct(b, coeffs, dtype, batch, thresh, x_out, ws, weights, st);
+    return e ? cuda_fail(e, "general reconstruction") : SHL_OK;
+  }
   const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
   float2* A = static_cast<float2*>(ws);
   float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
@@ -406,6 +504,10 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
   if (!x || !x_out) return fail(SHL_EINVAL, "x / x_out not accessible from the bank's device");
   DevGuard g(b->device);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (b->general) {
+    cudaError_t e = gen_shrink(b, x, mask, fest, batch, thresh, x_out, ws, st);
+    return e ? cuda_fail(e, "general shrink") : SHL_OK;
+  }
   const int N = b->N, M = b->M, K = b->K, Mh = b->Mh;
   const size_t img = align256((size_t)batch * plane_bytes(b));
   float2* X = static_cast<float2*>(ws);
@@ -452,6 +554,132 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
   return SHL_OK;
 }
 
+// ------------------------------------------------------- general path
+// Launch sequences of general.cu: full complex planes [N][M], so the staging
+// and spectrum planes are N * M * 8 bytes.  Same chunking as the
+// power-of-two path.
+cudaError_t gen_image_spectra(const shl_bank* b, shl::InMode mode, const float* x,
+                              const unsigned char* mask, const float* fest, int batch, float2* X,
+                              cudaStream_t st) {
+  namespace G = shl::gen;
+  const int N = b->N, M = b->M;
+  cudaError_t e;
+  {
+    Launch L_("gen_rows_fwd_image", st);
+    e = G::launch_rows_fwd(b->planM, mode == shl::IN_MASKED ? G::RIN_MASKED : G::RIN_F32, x, mask,
+                           fest, nullptr, X, N, batch, st);
+  }
+  if (e) return e;
+  for (int b0 = 0; b0 < batch; b0 += 65535) {
+    Launch L_("gen_cols_fwd_image", st);
+    e = G::launch_cols_fwd(b->planN, X + (size_t)b0 * N * M, M, std::min(65535, batch - b0), st);
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t gen_decompose(const shl_bank* b, shl::InMode mode, const float* x,
+                          const unsigned char* mask, const float* fest, int batch, void* coeffs,
+                          shl_dtype dtype, bool dual, void* ws, int S, cudaStream_t st) {
+  namespace G = shl::gen;
+  const int N = b->N, M = b->M, K = b->K;
+  float2* X = static_cast<float2*>(ws);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                        align256((size_t)batch * plane_bytes(b)));
+  cudaError_t e = gen_image_spectra(b, mode, x, mask, fest, batch, X, st);
+  if (e) return e;
+  const int total = batch * K;
+  const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  const float scale = (float)(1.0 / (double(N) * M));
+  S = std::min(S, 65535);
+  for (int s0 = 0; s0 < total; s0 += S) {
+    const int Sc = std::min(S, total - s0);
+    {
+      Launch L_("gen_cols_dec", st);
+      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, dual ? b->dInvWg : nullptr, M, K,
+                             s0, Sc, st);
+    }
+    if (e) return e;
+    {
+      Launch L_("gen_rows_inv_coeffs", st);
+      e = G::launch_rows_inv(b->planM, Z, static_cast<char*>(coeffs) + (size_t)s0 * N * M * esz,
+                             dtype == SHL_BF16, scale, N, Sc, st);
+    }
+    if (e) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t gen_reconstruct(const shl_bank* b, const void* coeffs, shl_dtype dtype, int batch,
+                            const float* thresh, float* x_out, void* ws, bool weights,
+                            cudaStream_t st) {
+  namespace G = shl::gen;
+  const int N = b->N, M = b->M, K = b->K;
+  float2* A = static_cast<float2*>(ws);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                        align256((size_t)batch * plane_bytes(b)));
+  const int total = batch * K, S = stage_subbands(b);
+  const size_t esz = dtype == SHL_BF16 ? 2 : 4;
+  cudaError_t e;
+  for (int s0 = 0; s0 < total;) {
+    const int Sc = next_chunk(s0, total, S, K);
+    {
+      Launch L_("gen_rows_fwd_coeffs", st);
+      e = G::launch_rows_fwd(b->planM, dtype == SHL_BF16 ? G::RIN_BF16 : G::RIN_F32,
+                             static_cast<const char*>(coeffs) + (size_t)s0 * N * M * esz, nullptr,
+                             nullptr, thresh ? thresh + s0 : nullptr, Z, N, Sc, st);
+    }
+    if (e) return e;
+    {
+      Launch L_("gen_cols_rec", st);
+      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, weights ? b->dInvWg : nullptr, M, K,
+                             s0, Sc, st);
+    }
+    if (e) return e;
+    s0 += Sc;
+  }
+  Launch L_("gen_rows_inv_image", st);
+  return G::launch_rows_inv(b->planM, A, x_out, false, (float)(1.0 / (double(N) * M)), N, batch,
+                            st);
+}
+
+cudaError_t gen_shrink(const shl_bank* b, const float* x, const unsigned char* mask,
+                       const float* fest, int batch, const float* thresh, float* x_out, void* ws,
+                       cudaStream_t st) {
+  namespace G = shl::gen;
+  const int N = b->N, M = b->M, K = b->K;
+  const size_t img = align256((size_t)batch * plane_bytes(b));
+  float2* X = static_cast<float2*>(ws);
+  float2* A = reinterpret_cast<float2*>(static_cast<char*>(ws) + img);
+  float2* Z = reinterpret_cast<float2*>(static_cast<char*>(ws) + 2 * img);
+  const float scale = (float)(1.0 / (double(N) * M));
+  cudaError_t e = gen_image_spectra(b, mask ? shl::IN_MASKED : shl::IN_F32, x, mask, fest, batch,
+                                    X, st);
+  if (e) return e;
+  const int total = batch * K, S = stage_subbands(b);
+  for (int s0 = 0; s0 < total;) {
+    const int Sc = next_chunk(s0, total, S, K);
+    {
+      Launch L_("gen_cols_dec", st);
+      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, nullptr, M, K, s0, Sc, st);
+    }
+    if (e) return e;
+    {
+      Launch L_("gen_rows_shrink", st);
+      e = G::launch_rows_shrink(b->planM, Z, thresh + s0, scale, N, Sc, st);
+    }
+    if (e) return e;
+    {
+      Launch L_("gen_cols_rec", st);
+      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, b->dInvWg, M, K, s0, Sc, st);
+    }
+    if (e) return e;
+    s0 += Sc;
+  }
+  Launch L_("gen_rows_inv_image", st);
+  return G::launch_rows_inv(b->planM, A, x_out, false, scale, N, batch, st);
+}
+
 }  // namespace
 
 namespace shl {
@@ -491,55 +719,93 @@ const char* shl_status_str(shl_status s) {
 
 const char* shl_last_error_detail(void) { return g_err.c_str(); }
 
+}  // extern "C"
+
+namespace {
+// Validates spectra in natural order: finite, and even (real spectra) or
+// Hermitian (complex): G(-k) = conj(G(k)), within 1e-9 of the largest
+// magnitude, so that real images give real coefficients.
+shl_status check_spectra(int N, int M, int K, const double* re, const double* im) {
+  for (int i = 0; i < K; ++i) {
+    const double* R = re + (size_t)i * N * M;
+    const double* I = im ? im + (size_t)i * N * M : nullptr;
+    double mx = 0.0, asym = 0.0;
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < M; ++x) {
+        const size_t e = (size_t)y * M + x, f = (size_t)((N - y) % N) * M + (M - x) % M;
+        const double a = R[e], ai = I ? I[e] : 0.0;
+        if (!std::isfinite(a) || !std::isfinite(ai)) return fail(SHL_EINVAL, "spectra must be finite");
+        mx = std::max(mx, std::hypot(a, ai));
+        asym = std::max(asym, std::hypot(a - R[f], I ? ai + I[f] : 0.0));
+      }
+    if (asym > 1e-9 * mx)
+      return fail(SHL_EINVAL, "spectrum " + std::to_string(i) +
+                                  (I ? " is not Hermitian: G(-k) != conj(G(k))"
+                                     : " is not even: G(-k) != G(k)"));
+  }
+  return SHL_OK;
+}
+
+shl_status make_bank(int N, int M, int K, std::vector<double>&& re, std::vector<double>&& im,
+                     std::vector<int>&& idx, bool general, int device, shl_bank** out) {
+  shl_bank* b = new shl_bank();
+  b->device = device; b->N = N; b->M = M; b->Mh = M / 2 + 1; b->K = K;
+  b->general = general;
+  b->cplx = !im.empty();
+  b->spectra = std::move(re);
+  b->spectra_im = std::move(im);
+  b->idx = std::move(idx);
+  b->idx.resize((size_t)K * 3, 0);
+  shl_status s = upload_bank(b);
+  if (s != SHL_OK) { free_bank(b); return s; }
+  *out = b;
+  return SHL_OK;
+}
+}  // namespace
+
+extern "C" {
+
 shl_status shl_bank_create_from_spectra(int rows, int cols, int K, const double* spectra,
                                         const int* idx, int device, shl_bank** out) {
   if (!out) return fail(SHL_EINVAL, "out is NULL");
   *out = nullptr;
-  shl_status s = check_size(rows, cols);
+  shl_status s = check_general_size(rows, cols);
   if (s != SHL_OK) return s;
   if (K < 1 || K > 4096 || !spectra) return fail(SHL_EINVAL, "need 1 <= K <= 4096 and spectra");
-  const int N = rows, M = cols;
-  for (int i = 0; i < K; ++i) {
-    const double* G = spectra + (size_t)i * N * M;
-    double mx = 0.0, asym = 0.0;
-    for (int y = 0; y < N; ++y)
-      for (int x = 0; x < M; ++x) {
-        const double a = G[(size_t)y * M + x], bb = G[(size_t)((N - y) % N) * M + (M - x) % M];
-        if (!std::isfinite(a)) return fail(SHL_EINVAL, "spectra must be finite");
-        mx = std::max(mx, std::fabs(a));
-        asym = std::max(asym, std::fabs(a - bb));
-      }
-    if (asym > 1e-9 * mx)
-      return fail(SHL_EINVAL, "spectrum " + std::to_string(i) + " is not even: G(-k) != G(k)");
-  }
-  shl_bank* b = new shl_bank();
-  b->device = device; b->N = N; b->M = M; b->Mh = M / 2 + 1; b->K = K;
-  b->spectra.assign(spectra, spectra + (size_t)K * N * M);
-  b->idx.assign((size_t)K * 3, 0);
-  if (idx) std::memcpy(b->idx.data(), idx, sizeof(int) * 3 * K);
-  s = upload_bank(b);
-  if (s != SHL_OK) { free_bank(b); return s; }
-  *out = b;
-  return SHL_OK;
+  if ((s = check_spectra(rows, cols, K, spectra, nullptr)) != SHL_OK) return s;
+  std::vector<int> ix(idx ? idx : nullptr, idx ? idx + 3 * (size_t)K : nullptr);
+  return make_bank(rows, cols, K, std::vector<double>(spectra, spectra + (size_t)K * rows * cols),
+                   {}, std::move(ix), !fast_size(rows, cols), device, out);
+}
+
+shl_status shl_bank_create_general(int rows, int cols, int K, const double* spectra_re,
+                                   const double* spectra_im, const int* idx, int device,
+                                   shl_bank** out) {
+  if (!out) return fail(SHL_EINVAL, "out is NULL");
+  *out = nullptr;
+  shl_status s = check_general_size(rows, cols);
+  if (s != SHL_OK) return s;
+  if (K < 1 || K > 4096 || !spectra_re) return fail(SHL_EINVAL, "need 1 <= K <= 4096 and spectra");
+  if ((s = check_spectra(rows, cols, K, spectra_re, spectra_im)) != SHL_OK) return s;
+  const size_t n = (size_t)K * rows * cols;
+  std::vector<int> ix(idx ? idx : nullptr, idx ? idx + 3 * (size_t)K : nullptr);
+  return make_bank(rows, cols, K, std::vector<double>(spectra_re, spectra_re + n),
+                   spectra_im ? std::vector<double>(spectra_im, spectra_im + n)
+                              : std::vector<double>(),
+                   std::move(ix), true, device, out);
 }
 
 shl_status shl_bank_create(int rows, int cols, int n_scales, const int* shear_levels, int full,
                            int device, shl_bank** out) {
   if (!out) return fail(SHL_EINVAL, "out is NULL");
   *out = nullptr;
-  shl_status s = check_size(rows, cols);
+  shl_status s = check_general_size(rows, cols);
   if (s != SHL_OK) return s;
   shl::HostBank hb;
   const char* msg = shl::build_shearlet_bank(rows, cols, n_scales, shear_levels, full, &hb);
   if (msg && *msg) return fail(SHL_EINVAL, msg);
-  shl_bank* b = new shl_bank();
-  b->device = device; b->N = rows; b->M = cols; b->Mh = cols / 2 + 1; b->K = hb.K;
-  b->spectra = std::move(hb.spectra);
-  b->idx = std::move(hb.idx);
-  s = upload_bank(b);
-  if (s != SHL_OK) { free_bank(b); return s; }
-  *out = b;
-  return SHL_OK;
+  return make_bank(rows, cols, hb.K, std::move(hb.spectra), {}, std::move(hb.idx),
+                   !fast_size(rows, cols), device, out);
 }
 
 shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shear_levels,
@@ -547,7 +813,9 @@ shl_status shl_bank_create_gpu(int rows, int cols, int n_scales, const int* shea
   if (!out) return fail(SHL_EINVAL, "out is NULL");
   *out = nullptr;
   shl_status s = check_size(rows, cols);
-  if (s != SHL_OK) return s;
+  if (s != SHL_OK)
+    return fail(SHL_EUNSUPPORTED, "shl_bank_create_gpu builds power-of-two sizes in [16, 2048]; "
+                                  "shl_bank_create builds the others on the host");
   if (device < 0) return fail(SHL_EINVAL, "shl_bank_create_gpu needs a device >= 0");
   std::vector<shl::BankItem> items;
   const char* err = shl::bank_items(n_scales, shear_levels, full, &items);
@@ -636,6 +904,20 @@ shl_status shl_bank_copy_info(const shl_bank* b, int* idx, double* rms, double* 
   if (rms) std::memcpy(rms, b->rms.data(), b->rms.size() * sizeof(double));
   if (spectra) std::memcpy(spectra, b->spectra.data(), b->spectra.size() * sizeof(double));
   if (dual_w) std::memcpy(dual_w, b->dual_w.data(), b->dual_w.size() * sizeof(double));
+  return SHL_OK;
+}
+
+shl_status shl_bank_path(const shl_bank* b, int* general) {
+  if (!b || !general) return fail(SHL_EINVAL, "bank and general must be non-NULL");
+  *general = b->general ? 1 : 0;
+  return SHL_OK;
+}
+
+shl_status shl_bank_copy_spectra_imag(const shl_bank* b, double* imag) {
+  if (!b || !imag) return fail(SHL_EINVAL, "bank and imag must be non-NULL");
+  const size_t n = (size_t)b->K * b->N * b->M;
+  if (b->cplx) std::memcpy(imag, b->spectra_im.data(), n * sizeof(double));
+  else std::memset(imag, 0, n * sizeof(double));
   return SHL_OK;
 }
 

@@ -87,7 +87,7 @@ struct Filters {
 };
 
 // In-place iterative radix-2 FFT of length n (power of two), sign -1 forward.
-void fft1d(cd* x, int n, int sign) {
+void fft_pow2(cd* x, int n, int sign) {
   for (int i = 1, j = 0; i < n; ++i) {
     int bit = n >> 1;
     for (; j & bit; bit >>= 1) j ^= bit;
@@ -105,6 +105,32 @@ void fft1d(cd* x, int n, int sign) {
       }
     }
   }
+}
+
+// Unnormalised DFT of any length n, in place (sign -1 forward).  Powers of
+// two go straight to fft_pow2; other lengths use Bluestein's identity
+// n k = (n^2 + k^2 - (k - n)^2) / 2, a circular convolution of length
+// m = the power of two >= 2n - 1 with the chirp exp(sign i pi t^2 / n).
+void fft1d(cd* x, int n, int sign) {
+  if ((n & (n - 1)) == 0) { fft_pow2(x, n, sign); return; }
+  int m = 1;
+  while (m < 2 * n - 1) m <<= 1;
+  std::vector<cd> c(n), a(m, cd(0.0, 0.0)), h(m, cd(0.0, 0.0));
+  for (int t = 0; t < n; ++t) {
+    const long long q = ((long long)t * t) % (2LL * n);
+    const double ang = sign * PI * (double)q / n;
+    c[t] = cd(std::cos(ang), std::sin(ang));
+  }
+  for (int t = 0; t < n; ++t) a[t] = x[t] * c[t];
+  for (int t = 0; t < n; ++t) {
+    h[t] = std::conj(c[t]);
+    if (t) h[m - t] = std::conj(c[t]);
+  }
+  fft_pow2(a.data(), m, -1);
+  fft_pow2(h.data(), m, -1);
+  for (int t = 0; t < m; ++t) a[t] *= h[t];
+  fft_pow2(a.data(), m, +1);
+  for (int t = 0; t < n; ++t) x[t] = c[t] * a[t] / (double)m;
 }
 
 // One cone-1 filter on an Nr x Mc grid (rows = x2/w2, cols = x1/w1).

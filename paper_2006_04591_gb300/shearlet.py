@@ -57,6 +57,9 @@ def lib():
         "shl_bank_create": (i, [i, i, i, vp, i, i, P(vp)]),
         "shl_bank_create_from_spectra": (i, [i, i, i, vp, vp, i, P(vp)]),
         "shl_bank_create_gpu": (i, [i, i, i, vp, i, i, P(vp)]),
+        "shl_bank_create_general": (i, [i, i, i, vp, vp, vp, i, P(vp)]),
+        "shl_bank_path": (i, [vp, P(i)]),
+        "shl_bank_copy_spectra_imag": (i, [vp, vp]),
         "shl_bank_destroy": (i, [vp]),
         "shl_bank_query": (i, [vp, P(i), P(i), P(i)]),
         "shl_bank_copy_info": (i, [vp, vp, vp, vp, vp]),
@@ -156,6 +159,39 @@ def shl_bank_create_from_spectra(spectra, idx=None, device=0):
            lib().shl_bank_create_from_spectra(N, M, K, S.ctypes.data_as(ctypes.c_void_p), ip,
                                               device, ctypes.byref(h)))
     return h
+
+
+def shl_bank_create_general(spectra, idx=None, device=0):
+    """Bank on the general kernels; ``spectra`` [K, N, M] real or complex
+    (Hermitian), natural order."""
+    S = np.asarray(spectra)
+    K, N, M = S.shape
+    re = np.ascontiguousarray(S.real, dtype=np.float64)
+    im = np.ascontiguousarray(S.imag, dtype=np.float64) if np.iscomplexobj(S) else None
+    ip = None
+    if idx is not None:
+        I = np.ascontiguousarray(idx, dtype=np.int32)
+        ip = I.ctypes.data_as(ctypes.c_void_p)
+    h = ctypes.c_void_p()
+    _check("shl_bank_create_general",
+           lib().shl_bank_create_general(N, M, K, re.ctypes.data_as(ctypes.c_void_p),
+                                         None if im is None else im.ctypes.data_as(ctypes.c_void_p),
+                                         ip, device, ctypes.byref(h)))
+    return h
+
+
+def shl_bank_path(h):
+    g = ctypes.c_int()
+    _check("shl_bank_path", lib().shl_bank_path(h, ctypes.byref(g)))
+    return g.value
+
+
+def shl_bank_copy_spectra_imag(h):
+    K, N, M = shl_bank_query(h)
+    out = np.zeros((K, N, M), np.float64)
+    _check("shl_bank_copy_spectra_imag",
+           lib().shl_bank_copy_spectra_imag(h, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
 
 
 def shl_bank_destroy(h):
@@ -258,6 +294,7 @@ class Bank:
         self.K, self.rows, self.cols = shl_bank_query(handle)
         info = shl_bank_copy_info(handle, spectra=False, dual_w=False)
         self.idx, self.rms = info["idx"], info["rms"]
+        self.general = bool(shl_bank_path(handle))
         self._rms_dev = None
 
     @classmethod
@@ -269,10 +306,21 @@ class Bank:
 
     @classmethod
     def from_spectra(cls, spectra, idx=None, device=0):
+        """Real, even spectra [K, N, M] in natural order (N, M in [1, 4096];
+        sizes other than powers of two in [16, 2048] use the general kernels)."""
         return cls(shl_bank_create_from_spectra(spectra, idx, device), device)
 
+    @classmethod
+    def from_complex_spectra(cls, spectra, idx=None, device=0):
+        """Spectra [K, N, M] (complex Hermitian, or real even) on the general
+        kernels, whatever the size."""
+        return cls(shl_bank_create_general(spectra, idx, device), device)
+
     def info(self):
-        return shl_bank_copy_info(self.handle)
+        d = shl_bank_copy_info(self.handle)
+        if self.general:
+            d["spectra_imag"] = shl_bank_copy_spectra_imag(self.handle)
+        return d
 
     def close(self):
         if self.handle is not None:

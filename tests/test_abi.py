@@ -33,11 +33,50 @@ def test_version_and_status_strings(L):
 
 def test_unsupported_sizes_rejected(L):
     h = ctypes.c_void_p()
-    for r, c in [(15, 16), (16, 24), (8, 16), (4096, 16), (16, 0)]:
+    for r, c in [(4097, 16), (16, 0), (0, 5), (16, 5000), (-3, 8)]:
         st = L.shl_bank_create(r, c, 2, None, 0, -1, ctypes.byref(h))
         assert st == 4 and not h.value
     st = L.shl_bank_create(16, 16, 2, None, 0, -1, None)
     assert st == 1
+    # the GPU builder covers the power-of-two sizes only; it rejects others
+    # before touching a device
+    st = L.shl_bank_create_gpu(15, 16, 2, None, 0, 0, ctypes.byref(h))
+    assert st == 4 and not h.value
+
+
+def test_bank_path_selection(L):
+    for (r, c, general) in [(16, 16, 0), (2048, 16, 0), (15, 16, 1), (8, 16, 1), (4096, 16, 1),
+                            (1, 1, 1), (17, 4093, 1)]:
+        G = np.ones((1, r, c))
+        h = S.shl_bank_create_from_spectra(G, device=-1)
+        assert S.shl_bank_path(h) == general
+        S.shl_bank_destroy(h)
+    h = S.shl_bank_create_general(np.ones((1, 16, 16)), device=-1)
+    assert S.shl_bank_path(h) == 1
+    S.shl_bank_destroy(h)
+
+
+def test_complex_bank_hermitian_check_and_info():
+    rng = np.random.default_rng(3)
+    g = rng.standard_normal((3, 9, 7))                     # real, non-symmetric filters
+    G = np.fft.fft2(g, axes=(-2, -1))                      # Hermitian spectra
+    h = S.shl_bank_create_general(G, idx=np.arange(9).reshape(3, 3), device=-1)
+    info = S.shl_bank_copy_info(h)
+    np.testing.assert_array_equal(info["spectra"], G.real)
+    np.testing.assert_array_equal(S.shl_bank_copy_spectra_imag(h), G.imag)
+    np.testing.assert_allclose(info["dual_w"], np.sum(np.abs(G) ** 2, axis=0), rtol=1e-14)
+    np.testing.assert_allclose(info["rms"], np.sqrt(np.sum(np.abs(G) ** 2, axis=(1, 2)) / 63),
+                               rtol=1e-14)
+    np.testing.assert_array_equal(info["idx"], np.arange(9).reshape(3, 3))
+    S.shl_bank_destroy(h)
+    bad = G.copy()
+    bad[1, 2, 3] += 0.5j                                   # breaks G(-k) = conj G(k)
+    with pytest.raises(S.ShearletError) as e:
+        S.shl_bank_create_general(bad, device=-1)
+    assert e.value.status == 1 and "Hermitian" in str(e.value)
+    # a real bank given to the complex entry point must still be even
+    with pytest.raises(S.ShearletError):
+        S.shl_bank_create_general(g, device=-1)
 
 
 def test_non_even_spectrum_rejected():
@@ -70,6 +109,9 @@ def test_host_only_bank_rejects_transform_calls(L):
 @pytest.mark.parametrize("rows,cols,J,levels,full", [
     (32, 32, 2, None, False), (64, 64, 3, None, False), (32, 64, 2, None, False),
     (64, 32, 2, [1, 2], True), (32, 32, 1, [0], False),
+    # general sizes: float64 Bluestein line DFTs in the host builder
+    (45, 60, 2, None, False), (33, 33, 1, None, True), (100, 72, 2, None, False),
+    (127, 128, 2, None, False), (7, 5, 1, None, False),
 ])
 def test_host_bank_builder_matches_oracle(rows, cols, J, levels, full):
     h = S.shl_bank_create(rows, cols, J, levels, full, device=-1)
