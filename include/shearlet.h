@@ -23,8 +23,8 @@
  * x[b][y][x].  rows and cols are in [1, 4096].  Powers of two in
  * [16, 2048] with real spectra run on the half-spectrum kernels; every other
  * size, and every bank with complex spectra, runs on the general kernels
- * (full complex planes, mixed-radix or Bluestein line DFTs; the same results
- * to float32 rounding, at a lower throughput).  Image
+ * (row-major half-spectrum planes, mixed-radix or Bluestein line DFTs; the
+ * same results to float32 rounding, at a lower throughput).  Image
  * arguments (x, x_out, f_masked, f_est, mask) may be device memory of the
  * bank's device, managed memory, or pinned host memory mapped into the
  * device's address space (cudaHostAlloc / cudaHostRegister): the first or
@@ -194,8 +194,7 @@ shl_status shl_bank_path(const shl_bank* bank, int* general);
  * per-image accumulators (reconstruct / adjoint) plus a staging area for
  * per-subband intermediates: up to 1 GiB of staging (e.g. all 784
  * subbands of 16 images at 512 x 512 with 49 filters).  A plane is
- * rows * (cols/2 + 1) complex float32 on the power-of-two path and
- * rows * cols complex float32 on the general path.  With the environment
+ * rows * (cols/2 + 1) complex float32 on both paths.  With the environment
  * variable SHL_PIPE=1 the power-of-two decomposition at rows = 512, cols in
  * {512, 1024} runs pipelined and stages 24 planes plus a few counters per 8
  * subbands instead.  Its contents on entry are ignored.

@@ -34,11 +34,11 @@ struct shl_bank {
   float2* dTw = nullptr;         // [TW_P]
   float* dRms = nullptr;         // [K]
   // General path (general.cu): full complex planes in natural order.
-  bool general = false;          // this bank runs on general.cu
+  bool general = false;          // this bank runs on general.cu (row-major half planes)
   bool cplx = false;             // complex spectra (imaginary parts kept)
   std::vector<double> spectra_im;  // [K][N][M] when cplx
-  void* dGg = nullptr;           // float [K][N][M], or float2 [K][N][M] when cplx
-  float* dInvWg = nullptr;       // [N][M]
+  void* dGg = nullptr;           // float [K][N][Mh], or float2 [K][N][Mh] when cplx
+  float* dInvWg = nullptr;       // [N][Mh]
   float2* dTab = nullptr;        // line tables of both plans
   shl::gen::LinePlan planN{}, planM{};
 };
@@ -135,11 +135,9 @@ int stage_subbands(const shl_bank* b) {
   return s < 1 ? 1 : s;
 }
 
-// Bytes of one spectrum plane: half spectrum on the power-of-two path, full
-// complex plane on the general path.
-size_t plane_bytes(const shl_bank* b) {
-  return (size_t)b->N * (b->general ? b->M : b->Mh) * sizeof(float2);
-}
+// Bytes of one half-spectrum plane (transposed [Mh][N] on the power-of-two
+// path, row-major [N][Mh] on the general path).
+size_t plane_bytes(const shl_bank* b) { return (size_t)b->N * b->Mh * sizeof(float2); }
 
 // Pipelined decomposition: chunk of CS subbands, NS ring slots.  Opt-in
 // (SHL_PIPE=1): it keeps the staging in L2 but measured slower than the
@@ -206,23 +204,26 @@ std::vector<float2> twiddle_table() {
 }
 
 // Tables of the general path: float32 filters (complex when the bank keeps
-// imaginary parts), 1/W, and the line plans of both axes.
+// imaginary parts) and 1/W on the half plane [N][Mh], and the line plans of
+// both axes.
 shl_status upload_general(shl_bank* b) {
-  const int N = b->N, M = b->M, K = b->K;
-  const size_t plane = (size_t)N * M;
+  const int N = b->N, M = b->M, Mh = b->Mh, K = b->K;
+  const size_t plane = (size_t)N * Mh;
   std::vector<float> hW(plane), hR(K);
-  for (size_t e = 0; e < plane; ++e) hW[e] = (float)(1.0 / b->dual_w[e]);
+  for (int y = 0; y < N; ++y)
+    for (int x = 0; x < Mh; ++x) hW[(size_t)y * Mh + x] = (float)(1.0 / b->dual_w[(size_t)y * M + x]);
   for (int i = 0; i < K; ++i) hR[i] = (float)b->rms[i];
   std::vector<float> hG;
   std::vector<float2> hGc;
-  if (b->cplx) {
-    hGc.resize((size_t)K * plane);
-    for (size_t e = 0; e < hGc.size(); ++e)
-      hGc[e] = make_float2((float)b->spectra[e], (float)b->spectra_im[e]);
-  } else {
-    hG.resize((size_t)K * plane);
-    for (size_t e = 0; e < hG.size(); ++e) hG[e] = (float)b->spectra[e];
-  }
+  if (b->cplx) hGc.resize((size_t)K * plane);
+  else hG.resize((size_t)K * plane);
+  for (int i = 0; i < K; ++i)
+    for (int y = 0; y < N; ++y)
+      for (int x = 0; x < Mh; ++x) {
+        const size_t d = ((size_t)i * N + y) * Mh + x, f = ((size_t)i * N + y) * M + x;
+        if (b->cplx) hGc[d] = make_float2((float)b->spectra[f], (float)b->spectra_im[f]);
+        else hG[d] = (float)b->spectra[f];
+      }
   shl::gen::LineTables tN = shl::gen::make_line_tables(N), tM = shl::gen::make_line_tables(M);
   const size_t gbytes = b->cplx ? hGc.size() * sizeof(float2) : hG.size() * sizeof(float);
   const size_t tabs = tN.data.size() + tM.data.size();
@@ -555,14 +556,14 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
 }
 
 // ------------------------------------------------------- general path
-// Launch sequences of general.cu: full complex planes [N][M], so the staging
-// and spectrum planes are N * M * 8 bytes.  Same chunking as the
+// Launch sequences of general.cu: row-major half-spectrum planes [N][Mh]
+// (N * Mh * 8 bytes, as on the power-of-two path).  Same chunking as the
 // power-of-two path.
 cudaError_t gen_image_spectra(const shl_bank* b, shl::InMode mode, const float* x,
                               const unsigned char* mask, const float* fest, int batch, float2* X,
                               cudaStream_t st) {
   namespace G = shl::gen;
-  const int N = b->N, M = b->M;
+  const int N = b->N, Mh = b->Mh;
   cudaError_t e;
   {
     Launch L_("gen_rows_fwd_image", st);
@@ -572,7 +573,7 @@ cudaError_t gen_image_spectra(const shl_bank* b, shl::InMode mode, const float* 
   if (e) return e;
   for (int b0 = 0; b0 < batch; b0 += 65535) {
     Launch L_("gen_cols_fwd_image", st);
-    e = G::launch_cols_fwd(b->planN, X + (size_t)b0 * N * M, M, std::min(65535, batch - b0), st);
+    e = G::launch_cols_fwd(b->planN, X + (size_t)b0 * N * Mh, Mh, std::min(65535, batch - b0), st);
     if (e) return e;
   }
   return cudaSuccess;
@@ -596,8 +597,8 @@ cudaError_t gen_decompose(const shl_bank* b, shl::InMode mode, const float* x,
     const int Sc = std::min(S, total - s0);
     {
       Launch L_("gen_cols_dec", st);
-      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, dual ? b->dInvWg : nullptr, M, K,
-                             s0, Sc, st);
+      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, dual ? b->dInvWg : nullptr, b->Mh,
+                             K, s0, Sc, st);
     }
     if (e) return e;
     {
@@ -632,8 +633,8 @@ cudaError_t gen_reconstruct(const shl_bank* b, const void* coeffs, shl_dtype dty
     if (e) return e;
     {
       Launch L_("gen_cols_rec", st);
-      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, weights ? b->dInvWg : nullptr, M, K,
-                             s0, Sc, st);
+      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, weights ? b->dInvWg : nullptr,
+                             b->Mh, K, s0, Sc, st);
     }
     if (e) return e;
     s0 += Sc;
@@ -661,7 +662,7 @@ cudaError_t gen_shrink(const shl_bank* b, const float* x, const unsigned char* m
     const int Sc = next_chunk(s0, total, S, K);
     {
       Launch L_("gen_cols_dec", st);
-      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, nullptr, M, K, s0, Sc, st);
+      e = G::launch_cols_dec(b->planN, X, Z, b->dGg, b->cplx, nullptr, b->Mh, K, s0, Sc, st);
     }
     if (e) return e;
     {
@@ -671,7 +672,7 @@ cudaError_t gen_shrink(const shl_bank* b, const float* x, const unsigned char* m
     if (e) return e;
     {
       Launch L_("gen_cols_rec", st);
-      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, b->dInvWg, M, K, s0, Sc, st);
+      e = G::launch_cols_rec(b->planN, Z, A, b->dGg, b->cplx, b->dInvWg, b->Mh, K, s0, Sc, st);
     }
     if (e) return e;
     s0 += Sc;

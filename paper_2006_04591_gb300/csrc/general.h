@@ -3,11 +3,14 @@
 // general.cu.
 //
 // The power-of-two kernels of fast.cu keep real, even spectra in transposed
-// half-spectrum planes.  This path keeps full complex planes [N][M] in
-// natural DFT order and computes every line DFT in shared memory with a
-// mixed-radix Stockham FFT (all prime factors <= 61), or with Bluestein's
-// chirp-z algorithm (a larger prime factor: the length-L DFT becomes a
-// circular convolution of length P = the power of two >= 2L - 1).
+// half-spectrum planes.  This path keeps row-major half-spectrum planes
+// [N][M/2+1] (columns kx = 0..M/2 of the natural-order spectrum; the rest
+// follows from Hermitian symmetry, which holds for real images and Hermitian
+// filters), complex filter values where the bank has them, and computes
+// every line DFT in shared memory with a mixed-radix Stockham FFT (all prime
+// factors <= 61), or with Bluestein's chirp-z algorithm (a larger prime
+// factor: the length-L DFT becomes a circular convolution of length P = the
+// power of two >= 2L - 1).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -51,12 +54,13 @@ void place_line_tables(LineTables* t, const float2* dev);
 // Real-row input of the forward row pass.
 enum RowIn : int { RIN_F32 = 0, RIN_BF16 = 1, RIN_MASKED = 2 };
 
-// Row passes on planes [nplanes][N][M] (rows of length M, plan pm).
+// Row passes (rows of length M, plan pm) between real planes [nplanes][N][M]
+// and half-spectrum planes [nplanes][N][M/2+1].
 //   rows_fwd:    real rows (thresholded on read when thresh != null, one
 //                threshold per plane; masked: mask ? f_masked : f_est) ->
-//                complex row DFTs out[nplanes][N][M].
-//   rows_inv:    complex rows -> inverse row DFT -> real part * scale ->
-//                float32 or bfloat16 out.
+//                row DFTs, columns 0..M/2 -> out.
+//   rows_inv:    Hermitian row spectra (from their halves) -> inverse row
+//                DFT -> real part * scale -> float32 or bfloat16 out.
 //   rows_shrink: in place: inverse row DFT -> real part * scale -> zero
 //                |c| < thresh[plane] -> forward row DFT.
 cudaError_t launch_rows_fwd(const LinePlan& pm, RowIn mode, const void* in, const uint8_t* mask,
@@ -67,7 +71,8 @@ cudaError_t launch_rows_inv(const LinePlan& pm, const float2* in, void* out, boo
 cudaError_t launch_rows_shrink(const LinePlan& pm, float2* z, const float* thresh, float scale,
                                int N, int nplanes, cudaStream_t st);
 
-// Column passes (columns of length N, plan pn) on planes of M columns.
+// Column passes (columns of length N, plan pn) on half-spectrum planes of
+// W = M/2 + 1 columns.
 //   cols_fwd: in-place forward column DFT of nplanes planes.
 //   cols_dec: T[s - s0] = inverse column DFT of G_i * X_b [* 1/W] for the
 //             subbands s = s0 .. s0+S-1 (b = s / K, i = s % K).
@@ -77,13 +82,14 @@ cudaError_t launch_rows_shrink(const LinePlan& pm, float2* z, const float* thres
 //             order of i; on the image's last subband acc is multiplied by
 //             1/W (when invW) and inverse column transformed into A_b, else
 //             stored there as the new partial sum.
-// G is float [K][N][M] (real spectra) or float2 [K][N][M] (complex).
-cudaError_t launch_cols_fwd(const LinePlan& pn, float2* X, int M, int nplanes, cudaStream_t st);
+// G is float [K][N][W] (real spectra) or float2 [K][N][W] (complex), 1/W
+// float [N][W]: the columns kx = 0..M/2 of the natural-order tables.
+cudaError_t launch_cols_fwd(const LinePlan& pn, float2* X, int W, int nplanes, cudaStream_t st);
 cudaError_t launch_cols_dec(const LinePlan& pn, const float2* X, float2* T, const void* G,
-                            bool cplx, const float* invW, int M, int K, int s0, int S,
+                            bool cplx, const float* invW, int W, int K, int s0, int S,
                             cudaStream_t st);
 cudaError_t launch_cols_rec(const LinePlan& pn, const float2* T, float2* A, const void* G,
-                            bool cplx, const float* invW, int M, int K, int s0, int S,
+                            bool cplx, const float* invW, int W, int K, int s0, int S,
                             cudaStream_t st);
 
 }  // namespace gen

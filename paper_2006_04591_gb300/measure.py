@@ -2,6 +2,7 @@
 
     python -m paper_2006_04591_gb300.measure [--out results/configs.json]
     python -m paper_2006_04591_gb300.measure --case N B
+    python -m paper_2006_04591_gb300.measure --general [--out FILE]
 
 ``--case N B`` runs only two decomposition + reconstruction passes of B
 cartoon images of N x N with the 4-scale bank (49 filters): the small case
@@ -17,6 +18,10 @@ fraction of the measured copy bandwidth.  Also the denoising time and PSNR
 at 16 x 512 x 512, the differentiable layer's forward + backward time at
 32 x 256 x 256 with bfloat16 coefficients, and the filter-bank construction
 time on the host and on the GPU.
+
+``--general`` times only the general kernels (sizes that are not powers of
+two, and the 512 x 512 bank forced onto them), with the per-launch-name
+device times of one pass from the library's own event profile.
 """
 
 from __future__ import annotations
@@ -84,6 +89,37 @@ def transform_point(bank, B, dtype, seed=5000):
             "peak_source": src, "pr_rel_err": float(((y - x).abs().max() / x.abs().max()).item())}
 
 
+def general_point(bank, B, label, seed=5000):
+    """transform_point on a general-kernel bank, plus the device time of
+    each launch name in one decomposition + reconstruction pass."""
+    from .shearlet import shl_profile_enable, shl_profile_read
+    out = dict(transform_point(bank, B, torch.float32, seed), config=label, general=bank.general)
+    x = torch.from_numpy(np.stack([synth.cartoon(bank.rows, bank.cols, seed + b)
+                                   for b in range(B)]).astype(np.float32)).cuda()
+    torch.cuda.synchronize()
+    shl_profile_read()
+    shl_profile_enable(1)
+    bank.reconstruct(bank.decompose(x))
+    torch.cuda.synchronize()
+    shl_profile_enable(0)
+    out["launch_ms"] = {k: round(v["ms"], 4) for k, v in shl_profile_read().items()}
+    return out
+
+
+def general_points():
+    pts = []
+    for (N, M) in ((480, 640), (500, 500), (509, 509)):
+        b = Bank.create(N, M, 4, device=0)
+        pts.append(general_point(b, 16, "%dx%d, K=49, B=16" % (N, M)))
+        b.close()
+    ref = Bank.create(512, 512, 4, device=0)
+    info = ref.info()
+    g = Bank.from_complex_spectra(info["spectra"], info["idx"], device=0)
+    pts.append(general_point(g, 16, "512x512 on the general kernels, K=49, B=16"))
+    pts.append(general_point(ref, 16, "512x512 on the half-spectrum kernels, K=49, B=16"))
+    return pts
+
+
 def small_case(N, B):
     bank = Bank.create(N, N, 4, device=0)
     x = torch.from_numpy(np.stack([synth.cartoon(N, N, s) for s in range(B)]).astype(np.float32)).cuda()
@@ -121,13 +157,22 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
     ap.add_argument("--case", type=int, nargs=2, metavar=("N", "B"), default=None)
+    ap.add_argument("--general", action="store_true")
     args = ap.parse_args()
     from . import _build
     _build.build()
     if args.case:
         small_case(*args.case)
         return
-    res = {"transform": [], "denoise": None, "layer": None, "bank": [], "inpainting": []}
+    if args.general:
+        pts = general_points()
+        print(json.dumps(pts, indent=1))
+        if args.out:
+            with open(args.out, "w") as fh:
+                json.dump(pts, fh, indent=1)
+        return
+    res = {"transform": [], "denoise": None, "layer": None, "bank": [], "inpainting": [],
+           "general": general_points()}
     for N, J in ((256, 2), (512, 4), (1024, 4)):
         res["bank"].append(bank_point(N, J))
     b256_2 = Bank.create(256, 256, 2, device=0)
