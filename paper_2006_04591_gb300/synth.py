@@ -26,6 +26,17 @@ Recipes (``numpy.random.default_rng(seed)``, PCG64):
   axis-aligned squares of side U{N/32..N/8}, top-left corners U[0, N-side]^2,
   set to 0 (missing); about 16 % of the pixels at the defaults.
 * ``gaussian_noise``: i.i.d. N(0, sigma^2).
+* ``shepp_logan``: the modified Shepp-Logan head phantom (Toft's published
+  table of ten ellipses, values in [0, 1]), the test object of Sec. 4.4,
+  on the square [-1, 1]^2 (row index = y).
+* ``random_ellipses``: the training objects of Sec. 4.4 ("randomly
+  generated ellipses"; the recipe is a reading): U{3..10} ellipses with
+  centre radius U[0, 0.6] at angle U[0, 2 pi), semi-axes U[0.05, 0.45],
+  rotation U[0, pi), value U[0.1, 0.6] and negative with probability 0.3,
+  summed and clipped to [0, 1].
+* ``ellipse_phantom``: pixel averages (``supersample``^2 point samples per
+  pixel) of a table of (value, a, b, x0, y0, alpha) ellipses on the
+  N x N grid of pixel side 2/N covering [-1, 1]^2.
 """
 
 from __future__ import annotations
@@ -178,3 +189,47 @@ def inpaint_batch(b: int = 8, n: int = 512, p: float = 0.5, seed0: int = 2000,
     else:
         mask = np.stack([bernoulli_mask(n, n, p, 50_000 + seed0 + i) for i in range(b)])
     return clean, mask, clean * mask
+
+
+# ------------------------------------------------------------ phantoms
+def shepp_logan():
+    """Rows (value, a, b, x0, y0, alpha [rad]) of the modified Shepp-Logan
+    phantom (Toft's table: the original's contrasts raised for display)."""
+    deg = np.pi / 180.0
+    return np.array([
+        [1.0, 0.69, 0.92, 0.0, 0.0, 0.0],
+        [-0.8, 0.6624, 0.874, 0.0, -0.0184, 0.0],
+        [-0.2, 0.11, 0.31, 0.22, 0.0, -18 * deg],
+        [-0.2, 0.16, 0.41, -0.22, 0.0, 18 * deg],
+        [0.1, 0.21, 0.25, 0.0, 0.35, 0.0],
+        [0.1, 0.046, 0.046, 0.0, 0.1, 0.0],
+        [0.1, 0.046, 0.046, 0.0, -0.1, 0.0],
+        [0.1, 0.046, 0.023, -0.08, -0.605, 0.0],
+        [0.1, 0.023, 0.023, 0.0, -0.606, 0.0],
+        [0.1, 0.023, 0.046, 0.06, -0.605, 0.0],
+    ])
+
+
+def random_ellipses(seed: int = 0):
+    """Ellipse table of one random training object (recipe in the module
+    docstring)."""
+    rng = np.random.default_rng(seed)
+    n = int(rng.integers(3, 11))
+    rad, ang = rng.uniform(0.0, 0.6, n), rng.uniform(0.0, 2 * np.pi, n)
+    val = rng.uniform(0.1, 0.6, n) * np.where(rng.random(n) < 0.3, -1.0, 1.0)
+    return np.stack([val, rng.uniform(0.05, 0.45, n), rng.uniform(0.05, 0.45, n),
+                     rad * np.cos(ang), rad * np.sin(ang), rng.uniform(0.0, np.pi, n)], axis=1)
+
+
+def ellipse_phantom(table, n: int, supersample: int = 2, clip: bool = True):
+    """Pixel averages of the ellipses of ``table`` on the n x n grid."""
+    h = 2.0 / n
+    q = (np.arange(n * supersample) + 0.5) * (h / supersample) - 1.0
+    Y, X = np.meshgrid(q, q, indexing="ij")
+    img = np.zeros_like(X)
+    for val, a, b, x0, y0, al in np.asarray(table, np.float64):
+        u = (X - x0) * np.cos(al) + (Y - y0) * np.sin(al)
+        v = -(X - x0) * np.sin(al) + (Y - y0) * np.cos(al)
+        img += val * ((u / a) ** 2 + (v / b) ** 2 <= 1.0)
+    img = img.reshape(n, supersample, n, supersample).mean(axis=(1, 3))
+    return np.clip(img, 0.0, 1.0) if clip else img
