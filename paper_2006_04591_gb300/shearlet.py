@@ -58,6 +58,11 @@ def lib():
         "shl_bank_create_from_spectra": (i, [i, i, i, vp, vp, i, P(vp)]),
         "shl_bank_create_gpu": (i, [i, i, i, vp, i, i, P(vp)]),
         "shl_bank_create_general": (i, [i, i, i, vp, vp, vp, i, P(vp)]),
+        "shl_ray_create": (i, [i, i, i, i, P(vp)]),
+        "shl_ray_destroy": (i, [vp]),
+        "shl_ray_query": (i, [vp, P(i), P(i), P(i)]),
+        "shl_ray_forward": (i, [vp, vp, i, vp, vp]),
+        "shl_ray_adjoint": (i, [vp, vp, i, vp, vp]),
         "shl_bank_path": (i, [vp, P(i)]),
         "shl_bank_copy_spectra_imag": (i, [vp, vp]),
         "shl_bank_destroy": (i, [vp]),
