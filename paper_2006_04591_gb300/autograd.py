@@ -5,6 +5,8 @@ ShearletDec: forward = shl_decompose (Sec. 3.4 decomposition),
 ShearletRec: forward = shl_reconstruct (Sec. 3.4 reconstruction),
              backward = shl_decompose with SHL_DUAL_WEIGHTED (its adjoint:
              decomposition with G_i / W).
+shearlet_dec_dual: forward = shl_decompose with SHL_DUAL_WEIGHTED (the
+             adjoint of the reconstruction), backward = shl_reconstruct.
 
 Both transforms are linear, so the backward passes are exact adjoints; no
 activations are saved.  Coefficients may be stored as bfloat16; gradients of
@@ -42,6 +44,22 @@ class _RecFn(torch.autograd.Function):
     def backward(ctx, gx):
         gc = ctx.bank.decompose(gx.contiguous().float(), dtype=ctx.c_dtype, dual=True)
         return gc, None
+
+
+class _DualDecFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x, bank: Bank):
+        ctx.bank = bank
+        return bank.decompose(x.contiguous().float(), dual=True)
+
+    @staticmethod
+    def backward(ctx, gc):
+        return ctx.bank.reconstruct(gc.contiguous()), None
+
+
+def shearlet_dec_dual(x: torch.Tensor, bank: Bank) -> torch.Tensor:
+    """[B, N, M] -> [B, K, N, M]: the adjoint of shearlet_rec (float32)."""
+    return _DualDecFn.apply(x, bank)
 
 
 def shearlet_dec(x: torch.Tensor, bank: Bank, dtype=torch.float32) -> torch.Tensor:

@@ -1,0 +1,236 @@
+"""Learned primal-dual CT reconstruction in the image and in the shearlet
+domain (Sec. 4.4, Algorithm 2).
+
+Forward operator: the parallel-beam ray transform R of ``csrc/ray.cu`` at 30
+angles (Sec. 4.4: "full angle, low-dose, 30 angles").  Iteration i = 1..I
+(I = 10) with primal memory f in X^Np and dual memory h in Y^Nd
+(Np = Nd = 5):
+
+  h <- h + Gamma_i([h, T(f^(2)), g])        dual net:   Nd + 2 -> 32 -> 32 -> Nd
+  f <- f + Lambda_i([f, T^*(h^(1))])         primal net: Np + 1 -> 32 -> 32 -> Np
+
+each net being Id + W3 A W2 A W1 with 3 x 3 convolutions W and PReLU A, and
+the result f^(1) after the last iteration.  In the image domain T = R / ||R||.
+In the shearlet domain every primal slot holds the K shearlet coefficients
+of an image as K channels ("each shearlet slice as a channel"), T =
+R SH^-1 / ||R SH^-1|| with SH^-1 the reconstruction of Sec. 3.4, its adjoint
+the dual-weighted decomposition of the back-projection, the primal net
+(Np + 1) K -> 32 -> 32 -> Np K, and the image SH^-1 f^(1).
+
+Readings (the paper gives the architecture but not the data protocol):
+* training objects: ``synth.random_ellipses`` phantoms, 128 x 128;
+* data: g = R f + e, e white Gaussian with standard deviation 5 % of the
+  mean |R f| of that object ("low dose");
+* f_0 = 0, h_0 = 0; loss: mean squared error against the object; Adam,
+  learning rate 1e-3 with cosine decay, batch 4;
+* test object: the modified Shepp-Logan phantom, PSNR with peak 1 and SSIM
+  (Wang et al. 2004: 11 x 11 Gaussian window, sigma 1.5, K1 = 0.01,
+  K2 = 0.03, data range 1), evaluated in float64 on the host.
+
+All convolutions, activations, the residual additions, the loss, Adam, the
+ray transform and the shearlet transforms run in this package's kernels;
+PyTorch holds the tensors, concatenates channels and records the graph.
+
+    python -m paper_2006_04591_gb300.lpd [--steps S] [--out results/lpd_128.json]
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import time
+
+import numpy as np
+import torch
+
+from . import nn as NN
+from . import synth
+from .autograd import shearlet_dec_dual, shearlet_rec
+from .ray import RayTransform, ray_adjoint, ray_forward
+from .shearlet import Bank
+
+
+class _Prox(torch.nn.Module):
+    """Id + W3 A W2 A W1 on [B, cin, H, W]; the identity acts on the first
+    cout input channels (the memory being updated)."""
+
+    def __init__(self, cin, cout, ch, gen, device, tc):
+        super().__init__()
+        self.cout, self.tc = cout, tc
+        dims = [cin, ch, ch, cout]
+        for l in range(3):
+            std = math.sqrt(2.0 / (dims[l] * 9)) * (0.1 if l == 2 else 1.0)
+            w = torch.randn((dims[l + 1], dims[l], 3, 3), generator=gen) * std
+            setattr(self, "w%d" % l, torch.nn.Parameter(w.to(device)))
+            setattr(self, "b%d" % l, torch.nn.Parameter(torch.zeros(dims[l + 1], device=device)))
+        self.a0 = torch.nn.Parameter(torch.full((1,), 0.25, device=device))
+        self.a1 = torch.nn.Parameter(torch.full((1,), 0.25, device=device))
+
+    def forward(self, x, mem):
+        h = NN.prelu(NN.conv3x3(x, self.w0, self.b0, self.tc), self.a0)
+        h = NN.prelu(NN.conv3x3(h, self.w1, self.b1, self.tc), self.a1)
+        return NN._ResidualAdd.apply(mem, NN.conv3x3(h, self.w2, self.b2, self.tc))
+
+
+class LPD(torch.nn.Module):
+    """Algorithm 2 of Sec. 4.4 with ``I`` unrolled iterations.
+
+    domain "image": primal memory [B, Np, N, N]; domain "shearlet": primal
+    memory [B, Np K, N, N] (slot j = channels j K .. j K + K - 1).
+    """
+
+    def __init__(self, op: RayTransform, domain="image", bank: Bank | None = None, iters=10,
+                 n_primal=5, n_dual=5, ch=32, seed=0, device="cuda", tc=True, scale=None):
+        super().__init__()
+        self.op, self.domain, self.bank = op, domain, bank
+        self.I, self.Np, self.Nd = iters, n_primal, n_dual
+        self.K = bank.K if domain == "shearlet" else 1
+        gen = torch.Generator().manual_seed(seed)
+        P = self.Np * self.K
+        self.primal = torch.nn.ModuleList(
+            [_Prox(P + self.K, P, ch, gen, device, tc) for _ in range(iters)])
+        self.dual = torch.nn.ModuleList(
+            [_Prox(self.Nd + 2, self.Nd, ch, gen, device, tc) for _ in range(iters)])
+        self.scale = float(scale) if scale is not None else 1.0 / self._op_norm()
+
+    # ----------------------------------------------------------- operators
+    def T(self, x):
+        """Primal slot [B, K, N, N] (K = 1: image) -> sinogram [B, 1, A, D]."""
+        img = shearlet_rec(x, self.bank) if self.domain == "shearlet" else x[:, 0]
+        return NN._Scale.apply(ray_forward(img.contiguous(), self.op), self.scale)[:, None]
+
+    def T_adj(self, y):
+        """Sinogram [B, 1, A, D] -> primal slot [B, K, N, N]."""
+        img = ray_adjoint(y[:, 0].contiguous(), self.op)
+        x = shearlet_dec_dual(img, self.bank) if self.domain == "shearlet" else img[:, None]
+        return NN._Scale.apply(x, self.scale)
+
+    @torch.no_grad()
+    def _op_norm(self, iters=40):
+        """||R|| or ||R SH^-1|| by power iteration on T^* T (unscaled)."""
+        self.scale = 1.0
+        g = torch.Generator(device="cuda").manual_seed(1)
+        x = torch.rand((1, self.K, self.op.n, self.op.n), device="cuda", generator=g)
+        lam = 1.0
+        for _ in range(iters):
+            y = self.T_adj(self.T(x))
+            lam = y.norm().item()
+            x = y / lam
+        return math.sqrt(lam)
+
+    # ------------------------------------------------------------- forward
+    def forward(self, g):
+        """g [B, A, D] -> reconstruction [B, N, N]."""
+        B, K, N = g.shape[0], self.K, self.op.n
+        gs = NN._Scale.apply(g.contiguous(), self.scale)[:, None]
+        f = torch.zeros((B, self.Np * K, N, N), device=g.device)
+        h = torch.zeros((B, self.Nd, self.op.n_angles, self.op.n_det), device=g.device)
+        for i in range(self.I):
+            h = self.dual[i](torch.cat([h, self.T(f[:, K:2 * K]), gs], dim=1), h)
+            f = self.primal[i](torch.cat([f, self.T_adj(h[:, 0:1])], dim=1), f)
+        first = f[:, 0:K].contiguous()
+        return shearlet_rec(first, self.bank) if self.domain == "shearlet" else first[:, 0]
+
+
+# -------------------------------------------------------------------- data
+def phantoms(n_obj, N, seed0):
+    return np.stack([synth.ellipse_phantom(synth.random_ellipses(seed0 + s), N)
+                     for s in range(n_obj)]).astype(np.float32)
+
+
+def noisy_data(op: RayTransform, f, gen, level=0.05):
+    """g = R f + e, e ~ N(0, (level * mean |R f|)^2) per object."""
+    with torch.no_grad():
+        p = op.forward(f)
+        sd = level * p.abs().mean(dim=(1, 2), keepdim=True)
+        return p + sd * torch.randn(p.shape, device=p.device, generator=gen)
+
+
+def psnr(x, ref):
+    mse = float(np.mean((np.asarray(x, np.float64) - np.asarray(ref, np.float64)) ** 2))
+    return 10.0 * math.log10(1.0 / mse)
+
+
+def ssim(x, ref, data_range=1.0):
+    """Mean SSIM with an 11 x 11 Gaussian window (sigma 1.5), float64."""
+    from scipy.ndimage import gaussian_filter
+    x, y = np.asarray(x, np.float64), np.asarray(ref, np.float64)
+    f = lambda a: gaussian_filter(a, 1.5, truncate=3.5, mode="constant")
+    mx, my = f(x), f(y)
+    sxx, syy, sxy = f(x * x) - mx * mx, f(y * y) - my * my, f(x * y) - mx * my
+    c1, c2 = (0.01 * data_range) ** 2, (0.03 * data_range) ** 2
+    m = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
+    return float(m[5:-5, 5:-5].mean())
+
+
+# ---------------------------------------------------------------- training
+def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=0, scales=2,
+          log_every=100):
+    op = RayTransform(N, A, device=0)
+    bank = Bank.create(N, N, scales, device=0) if domain == "shearlet" else None
+    net = LPD(op, domain, bank, seed=seed)
+    opt = NN.Adam(net.parameters(), lr=lr)
+    pool = torch.from_numpy(phantoms(n_train, N, 10_000)).cuda()
+    gen = torch.Generator(device="cuda").manual_seed(seed + 7)
+    rng = np.random.default_rng(seed)
+    hist, t_steps = [], []
+    for it in range(steps):
+        opt.lr = 0.5 * lr * (1.0 + math.cos(math.pi * it / steps))
+        idx = torch.from_numpy(rng.integers(0, n_train, batch)).cuda()
+        f_true = pool[idx].contiguous()
+        g = noisy_data(op, f_true, gen)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        opt.zero_grad()
+        loss = NN.mse(net(g), f_true)
+        loss.backward()
+        opt.step()
+        torch.cuda.synchronize()
+        t_steps.append(time.perf_counter() - t0)
+        if it % log_every == 0 or it == steps - 1:
+            hist.append((it, float(loss.item())))
+    return net, op, bank, hist, t_steps
+
+
+@torch.no_grad()
+def evaluate(net, op, N=128, seed=123):
+    f = synth.ellipse_phantom(synth.shepp_logan(), N, supersample=4).astype(np.float32)
+    ft = torch.from_numpy(f)[None].cuda()
+    gen = torch.Generator(device="cuda").manual_seed(seed)
+    g = noisy_data(op, ft, gen)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    out = net(g)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    rec = out[0].cpu().numpy()
+    return {"psnr": psnr(rec, f), "ssim": ssim(rec, f), "reconstruct_ms": dt * 1e3}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--out", default=None)
+    args = ap.parse_args()
+    from . import _build
+    _build.build()
+    res = {"size": 128, "angles": 30, "iterations": 10, "n_primal": 5, "n_dual": 5,
+           "batch": args.batch, "train_steps": args.steps, "noise": "5% of mean |Rf|"}
+    for domain in ("image", "shearlet"):
+        net, op, bank, hist, ts = train(domain, steps=args.steps, batch=args.batch)
+        ev = evaluate(net, op)
+        res[domain] = dict(ev, loss=hist, ms_per_train_step=1e3 * float(np.median(ts[5:])),
+                           filters=bank.K if bank else None,
+                           parameters=int(sum(p.numel() for p in net.parameters())))
+        print(domain, json.dumps(res[domain]["psnr"]), res[domain]["ssim"],
+              res[domain]["ms_per_train_step"])
+    print(json.dumps({k: v for k, v in res.items()}, indent=1))
+    if args.out:
+        with open(args.out, "w") as fh:
+            json.dump(res, fh, indent=1)
+
+
+if __name__ == "__main__":
+    main()

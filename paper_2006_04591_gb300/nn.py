@@ -151,9 +151,20 @@ def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False, tc_w=False):
         shl_nn_conv3x3_backward_weight_tc(x, gout, gw, gb)
     ws = _ws(L.shl_nn_conv3x3_workspace_floats(B, Ci, Co, H, W), x) if (not tc_w or
                                                                       (need_gin and not tc)) else None
-    if not tc_w:
+    if not tc_w and Ci <= 64:
         _chk("conv3x3_backward_weight", L.shl_nn_conv3x3_backward_weight(
             _p(x), _p(gout), _p(gw), _p(gb), B, Ci, Co, H, W, _p(ws), _st(x)))
+    elif not tc_w:
+        # the kernel stages at most 64 input channels of a tile; the weight
+        # gradient of an input-channel group depends on that group only
+        for c0 in range(0, Ci, 64):
+            c1 = min(Ci, c0 + 64)
+            xg = x[:, c0:c1].contiguous()
+            gwg = torch.empty((Co, c1 - c0, 3, 3), dtype=torch.float32, device=x.device)
+            wsg = _ws(L.shl_nn_conv3x3_workspace_floats(B, c1 - c0, Co, H, W), x)
+            _chk("conv3x3_backward_weight", L.shl_nn_conv3x3_backward_weight(
+                _p(xg), _p(gout), _p(gwg), _p(gb), B, c1 - c0, Co, H, W, _p(wsg), _st(x)))
+            gw[:, c0:c1] = gwg
     gin = None
     if need_gin:
         gin = torch.empty_like(x)
@@ -355,6 +366,25 @@ class _ResidualAdd(torch.autograd.Function):
     @staticmethod
     def backward(ctx, g):
         return g, g
+
+
+class _Scale(torch.autograd.Function):
+    """alpha * x (a python float alpha) through shl_nn_axpy into zeros."""
+
+    @staticmethod
+    def forward(ctx, x, alpha):
+        ctx.alpha = float(alpha)
+        x = x.contiguous()
+        y = torch.zeros_like(x)
+        _chk("axpy", lib().shl_nn_axpy(_p(x), ctx.alpha, _p(y), x.numel(), _st(x)))
+        return y
+
+    @staticmethod
+    def backward(ctx, g):
+        g = g.contiguous()
+        gx = torch.zeros_like(g)
+        _chk("axpy", lib().shl_nn_axpy(_p(g), ctx.alpha, _p(gx), g.numel(), _st(g)))
+        return gx, None
 
 
 def conv3x3(x, w, b, tc=False):
