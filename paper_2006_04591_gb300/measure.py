@@ -120,6 +120,23 @@ def general_points():
     return pts
 
 
+def ray_point(N, A, B):
+    """Forward and adjoint ray transform of B phantoms (CUDA-event timing),
+    as samples (rays x samples per ray) per second."""
+    from .ray import RayTransform
+    op = RayTransform(N, A, device=0)
+    x = torch.from_numpy(np.stack([synth.ellipse_phantom(synth.random_ellipses(s), N)
+                                   for s in range(B)]).astype(np.float32)).cuda()
+    p = op.forward(x)
+    y = torch.empty_like(x)
+    tf = _time(lambda: op.forward(x, out=p))
+    ta = _time(lambda: op.adjoint(p, out=y))
+    samples = B * A * op.n_det * N
+    return {"size": N, "angles": A, "bins": op.n_det, "batch": B, "forward_ms": tf * 1e3,
+            "adjoint_ms": ta * 1e3, "forward_samples_per_s": samples / tf,
+            "adjoint_samples_per_s": samples / ta}
+
+
 def small_case(N, B):
     bank = Bank.create(N, N, 4, device=0)
     x = torch.from_numpy(np.stack([synth.cartoon(N, N, s) for s in range(B)]).astype(np.float32)).cuda()
@@ -158,11 +175,19 @@ def main():
     ap.add_argument("--out", default=None)
     ap.add_argument("--case", type=int, nargs=2, metavar=("N", "B"), default=None)
     ap.add_argument("--general", action="store_true")
+    ap.add_argument("--ray", action="store_true")
     args = ap.parse_args()
     from . import _build
     _build.build()
     if args.case:
         small_case(*args.case)
+        return
+    if args.ray:
+        pts = [ray_point(128, 30, 32), ray_point(512, 180, 8), ray_point(1024, 360, 1)]
+        print(json.dumps(pts, indent=1))
+        if args.out:
+            with open(args.out, "w") as fh:
+                json.dump(pts, fh, indent=1)
         return
     if args.general:
         pts = general_points()
@@ -172,7 +197,8 @@ def main():
                 json.dump(pts, fh, indent=1)
         return
     res = {"transform": [], "denoise": None, "layer": None, "bank": [], "inpainting": [],
-           "general": general_points()}
+           "general": general_points(),
+           "ray": [ray_point(128, 30, 32), ray_point(512, 180, 8), ray_point(1024, 360, 1)]}
     for N, J in ((256, 2), (512, 4), (1024, 4)):
         res["bank"].append(bank_point(N, J))
     b256_2 = Bank.create(256, 256, 2, device=0)
