@@ -21,8 +21,9 @@ Readings (the paper gives the architecture but not the data protocol):
 * training objects: ``synth.random_ellipses`` phantoms, 128 x 128;
 * data: g = R f + e, e white Gaussian with standard deviation 5 % of the
   mean |R f| of that object ("low dose");
-* f_0 = 0, h_0 = 0; loss: mean squared error against the object; Adam,
-  learning rate 1e-3 with cosine decay, batch 4;
+* f_0 = 0, h_0 = 0; loss: mean squared error against the object; Adam
+  (beta2 = 0.99), learning rate 1e-3 with cosine decay, the gradient's
+  global norm clipped to 1, batch 4;
 * test object: the modified Shepp-Logan phantom, PSNR with peak 1 and SSIM
   (Wang et al. 2004: 11 x 11 Gaussian window, sigma 1.5, K1 = 0.01,
   K2 = 0.03, data range 1), evaluated in float64 on the host.
@@ -170,7 +171,8 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
     op = RayTransform(N, A, device=0)
     bank = Bank.create(N, N, scales, device=0) if domain == "shearlet" else None
     net = LPD(op, domain, bank, seed=seed)
-    opt = NN.Adam(net.parameters(), lr=lr)
+    params = list(net.parameters())
+    opt = NN.Adam(params, lr=lr, betas=(0.9, 0.99))
     pool = torch.from_numpy(phantoms(n_train, N, 10_000)).cuda()
     gen = torch.Generator(device="cuda").manual_seed(seed + 7)
     rng = np.random.default_rng(seed)
@@ -185,6 +187,7 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
         opt.zero_grad()
         loss = NN.mse(net(g), f_true)
         loss.backward()
+        NN.clip_grad_norm(params, 1.0)
         opt.step()
         torch.cuda.synchronize()
         t_steps.append(time.perf_counter() - t0)

@@ -22,6 +22,7 @@ from __future__ import annotations
 import ctypes
 import math
 
+import numpy as np
 import torch
 
 from . import shearlet as S
@@ -512,6 +513,34 @@ class CoeffNet(torch.nn.Module):
         h = prelu(conv3x3(c, self.w0, self.b0, self.tc), self.a0)
         h = prelu(conv3x3(h, self.w1, self.b1, self.tc), self.a1)
         return _ResidualAdd.apply(c, conv3x3(h, self.w2, self.b2, self.tc))
+
+
+@torch.no_grad()
+def clip_grad_norm(params, max_norm):
+    """Scale the gradients of ``params`` so that their global 2-norm is at
+    most ``max_norm``; returns the norm before clipping.  The gradients are
+    gathered into one flat buffer; its sum of squares comes from
+    shl_nn_mse_forward against zeros and the scaling from shl_nn_axpy (the
+    parameters' gradients then become views of the scaled buffer)."""
+    L = lib()
+    ps = [p for p in params if p.grad is not None]
+    if not ps:
+        return 0.0
+    flat = torch.cat([p.grad.reshape(-1) for p in ps])
+    n = flat.numel()
+    zero = torch.zeros_like(flat)
+    sq = torch.empty(1, dtype=torch.float32, device=flat.device)
+    ws = _ws(L.shl_nn_reduce_workspace_floats(n), flat)
+    _chk("mse_forward", L.shl_nn_mse_forward(_p(flat), _p(zero), _p(sq), n, _p(ws), _st(flat)))
+    total = math.sqrt(float(sq.item()))
+    if total > max_norm:
+        _chk("axpy", L.shl_nn_axpy(_p(flat), max_norm / total, _p(zero), n, _st(flat)))
+        off = 0
+        for p in ps:
+            k = p.grad.numel()
+            p.grad = zero[off:off + k].view_as(p.grad)
+            off += k
+    return total
 
 
 class Adam:

@@ -105,3 +105,18 @@ def test_weight_gradient_with_more_than_64_input_channels():
     for got, want in ((wg.grad, wt.grad), (bg.grad, bt.grad), (xg.grad, xt.grad)):
         g, r = got.cpu().numpy(), want.numpy()
         assert np.abs(g - r).max() <= 1e-4 * np.abs(r).max()
+
+
+def test_clip_grad_norm():
+    from paper_2006_04591_gb300 import nn as NN
+    g = torch.Generator(device="cuda").manual_seed(0)
+    ps = [torch.nn.Parameter(torch.zeros(s, device="cuda")) for s in ((3, 5), (7,), (2, 2, 3, 3))]
+    for p in ps:
+        p.grad = torch.randn(p.shape, device="cuda", generator=g)
+    want = np.sqrt(sum(float((p.grad.double() ** 2).sum()) for p in ps))
+    before = [p.grad.clone() for p in ps]
+    assert abs(NN.clip_grad_norm(ps, 10 * want) - want) <= 1e-5 * want
+    assert all(torch.equal(a, p.grad) for a, p in zip(before, ps))     # below the limit
+    NN.clip_grad_norm(ps, 0.5)
+    after = np.sqrt(sum(float((p.grad.double() ** 2).sum()) for p in ps))
+    assert abs(after - 0.5) <= 1e-5
