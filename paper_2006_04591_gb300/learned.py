@@ -13,7 +13,7 @@ adjoint transforms (shl_adjoint for the decomposition, the dual-weighted
 decomposition for the reconstruction) and the library's network kernels.
 Inference uses the hard threshold through shl_decompose_masked and
 shl_reconstruct, i.e. exactly the plain method's kernels with learned
-thresholds.  The plain loop stays as fallback and as the judge of PSNR.
+thresholds.  The plain loop stays as fallback and as the PSNR reference.
 
 Run ``python -m paper_2006_04591_gb300.learned`` to train on 2,000 seeded
 512 x 512 pairs and compare with the plain method on 8 held-out images.
