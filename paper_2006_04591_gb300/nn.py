@@ -178,6 +178,82 @@ def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False, tc_w=False):
 
 
 # ------------------------------------------------------------- autograd
+# Channel groups for the tensor-core kernels (conv3x3(..., tc="grouped")):
+# one call takes at most 48 input and 48 output channels (weight gradient: 42
+# input channels, 3 Ci <= 128).  Wider layers run as a sum over input-channel
+# groups (partials added by shl_nn_axpy) for each output-channel group; a
+# layer within the limits is a single call.
+TC_CH, TC_WCH = 48, 42
+
+
+def _groups(n, g):
+    return [(a, min(n, a + g)) for a in range(0, n, g)]
+
+
+def _tc_width_ok(H, W):
+    return H >= 1 and W >= 128 and W % 128 == 0
+
+
+def _axpy(src, dst, alpha=1.0):
+    _chk("axpy", lib().shl_nn_axpy(_p(src), float(alpha), _p(dst), src.numel(), _st(dst)))
+
+
+def conv3x3_forward_tc_grouped(x, w, b, out):
+    B, Ci, H, W = x.shape
+    Co = w.shape[0]
+    cig, cog = _groups(Ci, TC_CH), _groups(Co, TC_CH)
+    xs = [x if len(cig) == 1 else x[:, a:c].contiguous() for a, c in cig]
+    for o0, o1 in cog:
+        dst = out if len(cog) == 1 else torch.empty((B, o1 - o0, H, W), device=x.device)
+        for k, (a, c) in enumerate(cig):
+            wg = w[o0:o1, a:c].contiguous()
+            if k == 0:
+                shl_nn_conv3x3_forward_tc(xs[k], wg, b[o0:o1].contiguous(), dst)
+            else:
+                part = torch.empty_like(dst)
+                shl_nn_conv3x3_forward_tc(xs[k], wg, None, part)
+                _axpy(part, dst)
+        if len(cog) > 1:
+            out[:, o0:o1] = dst
+
+
+def conv3x3_backward_data_tc_grouped(gout, w, gin):
+    B, Ci, H, W = gin.shape
+    Co = w.shape[0]
+    cig, cog = _groups(Ci, TC_CH), _groups(Co, TC_CH)
+    gos = [gout if len(cog) == 1 else gout[:, o0:o1].contiguous() for o0, o1 in cog]
+    for a, c in cig:
+        dst = gin if len(cig) == 1 else torch.empty((B, c - a, H, W), device=gin.device)
+        for k, (o0, o1) in enumerate(cog):
+            wg = w[o0:o1, a:c].contiguous()
+            if k == 0:
+                shl_nn_conv3x3_backward_data_tc(gos[k], wg, dst)
+            else:
+                part = torch.empty_like(dst)
+                shl_nn_conv3x3_backward_data_tc(gos[k], wg, part)
+                _axpy(part, dst)
+        if len(cig) > 1:
+            gin[:, a:c] = dst
+
+
+def conv3x3_backward_weight_tc_grouped(x, gout, gw, gb):
+    Ci, Co = x.shape[1], gout.shape[1]
+    cig, cog = _groups(Ci, TC_WCH), _groups(Co, TC_CH)
+    if len(cig) == 1 and len(cog) == 1:
+        shl_nn_conv3x3_backward_weight_tc(x, gout, gw, gb)
+        return
+    xs = [x[:, a:c].contiguous() for a, c in cig]
+    for o0, o1 in cog:
+        go = gout[:, o0:o1].contiguous()
+        for k, (a, c) in enumerate(cig):
+            gwg = torch.empty((o1 - o0, c - a, 3, 3), device=x.device)
+            gbg = torch.empty(o1 - o0, device=x.device)
+            shl_nn_conv3x3_backward_weight_tc(xs[k], go, gwg, gbg)
+            gw[o0:o1, a:c] = gwg
+            if k == 0:
+                gb[o0:o1] = gbg
+
+
 class _Conv3x3(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x, w, b, tc):
@@ -186,7 +262,13 @@ class _Conv3x3(torch.autograd.Function):
                           device=x.device)
         B, Ci, H, W = x.shape
         Co = w.shape[0]
-        # tensor cores for the forward and the input gradient where the shape allows
+        ctx.grouped = tc == "grouped" and _tc_width_ok(H, W)
+        if ctx.grouped:
+            # every pass on the tensor cores, in channel groups
+            conv3x3_forward_tc_grouped(x, w.contiguous(), b.contiguous(), out)
+            ctx.save_for_backward(x, w)
+            return out
+        # tensor cores for each pass where one call takes the shape
         ctx.tc_fwd = bool(tc) and shl_nn_conv3x3_tc_supported(Ci, Co, H, W)
         ctx.tc_bwd = bool(tc) and shl_nn_conv3x3_tc_supported(Co, Ci, H, W)
         ctx.tc_w = bool(tc) and shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)
@@ -200,9 +282,19 @@ class _Conv3x3(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gout):
         x, w = ctx.saved_tensors
-        gin, gw, gb = shl_nn_conv3x3_backward(x, w.contiguous(), gout.contiguous(),
-                                             ctx.needs_input_grad[0], tc=ctx.tc_bwd,
-                                             tc_w=ctx.tc_w)
+        gout = gout.contiguous()
+        w = w.contiguous()
+        if not ctx.grouped:
+            gin, gw, gb = shl_nn_conv3x3_backward(x, w, gout, ctx.needs_input_grad[0],
+                                                 tc=ctx.tc_bwd, tc_w=ctx.tc_w)
+            return gin, gw, gb, None
+        gw = torch.empty_like(w)
+        gb = torch.empty(w.shape[0], dtype=torch.float32, device=x.device)
+        conv3x3_backward_weight_tc_grouped(x, gout, gw, gb)
+        gin = None
+        if ctx.needs_input_grad[0]:
+            gin = torch.empty_like(x)
+            conv3x3_backward_data_tc_grouped(gout, w, gin)
         return gin, gw, gb, None
 
 
@@ -391,7 +483,10 @@ class _Scale(torch.autograd.Function):
 def conv3x3(x, w, b, tc=False):
     """3x3 convolution; tc=True runs the forward, the input gradient and the
     weight gradient on the tensor cores (bfloat16 operands, float32
-    accumulation) where the shapes are supported, else the float32 kernels."""
+    accumulation) where one call takes the shape, else the float32 kernels;
+    tc="grouped" runs every pass on the tensor cores whenever the row width
+    is a multiple of 128, in channel groups for wider layers (measured slower
+    for the learned primal-dual networks, whose steps are bound by launches)."""
     return _Conv3x3.apply(x, w, b, tc)
 
 

@@ -169,3 +169,32 @@ def test_warp_specialised_conv_matches_rounded_oracle():
                        text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "ws ok" in r.stdout
+
+
+@pytest.mark.parametrize("B,Ci,Co,H,W", [(2, 102, 32, 3, 128), (1, 32, 85, 4, 128),
+                                         (1, 102, 85, 2, 256), (2, 7, 32, 3, 256)])
+def test_grouped_tc_conv_autograd_matches_rounded_oracle(B, Ci, Co, H, W):
+    # layers wider than one tensor-core call (the shearlet-domain primal
+    # networks of the learned primal-dual reconstruction): channel groups
+    from paper_2006_04591_gb300 import nn
+    gen = torch.Generator().manual_seed(Ci * 100 + Co)
+    x = torch.randn((B, Ci, H, W), generator=gen)
+    w = torch.randn((Co, Ci, 3, 3), generator=gen) * 0.1
+    b = torch.randn(Co, generator=gen)
+    go = torch.randn((B, Co, H, W), generator=gen)
+    xg = x.cuda().requires_grad_(True)
+    wg = w.cuda().requires_grad_(True)
+    bg = b.cuda().requires_grad_(True)
+    y = nn.conv3x3(xg, wg, bg, tc="grouped")
+    (y * go.cuda()).sum().backward()
+    nn.shl_nn_tc_status()
+    assert _rel(y, ON.conv3x3(_bf(x), _bf(w), b.double())) <= TOL
+    # input gradient: rounded gout and w; weight gradient: rounded x and gout
+    xo = torch.zeros((B, Ci, H, W), dtype=torch.float64, requires_grad=True)
+    (ON.conv3x3(xo, _bf(w), torch.zeros(Co, dtype=torch.float64)) * _bf(go)).sum().backward()
+    assert _rel(xg.grad, xo.grad) <= TOL
+    wo = torch.zeros((Co, Ci, 3, 3), dtype=torch.float64, requires_grad=True)
+    (ON.conv3x3(_bf(x), wo, None) * _bf(go)).sum().backward()
+    assert _rel(wg.grad, wo.grad) <= TOL
+    # the bias gradient sums the float32 (unrounded) output gradient
+    assert _rel(bg.grad, go.double().sum((0, 2, 3))) <= 1e-5
