@@ -40,6 +40,7 @@ from __future__ import annotations
 import argparse
 import json
 import math
+import os
 import time
 
 import numpy as np
@@ -167,7 +168,11 @@ def ssim(x, ref, data_range=1.0):
 
 # ---------------------------------------------------------------- training
 def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=0, scales=2,
-          log_every=100):
+          log_every=100, checkpoint=None):
+    """Train the ``domain`` network for ``steps`` steps.  With ``checkpoint``
+    (a file path) an existing checkpoint is resumed (parameters, Adam state,
+    step; the data stream restarts at that step's seeds) and the final state
+    is written there."""
     op = RayTransform(N, A, device=0)
     bank = Bank.create(N, N, scales, device=0) if domain == "shearlet" else None
     net = LPD(op, domain, bank, seed=seed)
@@ -177,7 +182,12 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
     gen = torch.Generator(device="cuda").manual_seed(seed + 7)
     rng = np.random.default_rng(seed)
     hist, t_steps = [], []
-    for it in range(steps):
+    start = 0
+    if checkpoint is not None and os.path.exists(checkpoint):
+        start, _ = NN.load_checkpoint(checkpoint, net, opt)
+        rng = np.random.default_rng([seed, start])
+        gen = torch.Generator(device="cuda").manual_seed(seed + 7 + 1000003 * start)
+    for it in range(start, steps):
         opt.lr = 0.5 * lr * (1.0 + math.cos(math.pi * it / steps))
         idx = torch.from_numpy(rng.integers(0, n_train, batch)).cuda()
         f_true = pool[idx].contiguous()
@@ -193,6 +203,9 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
         t_steps.append(time.perf_counter() - t0)
         if it % log_every == 0 or it == steps - 1:
             hist.append((it, float(loss.item())))
+    if checkpoint is not None:
+        NN.save_checkpoint(checkpoint, net, opt, step=steps,
+                           meta={"domain": domain, "size": N, "angles": A, "scales": scales})
     return net, op, bank, hist, t_steps
 
 

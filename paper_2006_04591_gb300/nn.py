@@ -638,6 +638,50 @@ def clip_grad_norm(params, max_norm):
     return total
 
 
+CHECKPOINT_VERSION = 1
+
+
+def save_checkpoint(path, module, opt=None, step=0, meta=None):
+    """Versioned checkpoint: the module's parameters and buffers, the Adam
+    state (moments, step count, hyper-parameters) and free-form metadata,
+    written atomically (temporary file, then rename)."""
+    import os
+    state = {"version": CHECKPOINT_VERSION, "step": int(step), "meta": meta or {},
+             "module": {k: v.detach().cpu() for k, v in module.state_dict().items()}}
+    if opt is not None:
+        state["adam"] = {"m": [m.cpu() for m in opt.m], "v": [v.cpu() for v in opt.v],
+                         "step_count": opt.step_count, "lr": opt.lr, "b1": opt.b1,
+                         "b2": opt.b2, "eps": opt.eps}
+    tmp = str(path) + ".tmp"
+    torch.save(state, tmp)
+    os.replace(tmp, path)
+
+
+def load_checkpoint(path, module, opt=None):
+    """Restore a checkpoint written by save_checkpoint into ``module`` (and
+    ``opt``); returns (step, meta).  Raises ValueError on a version or shape
+    mismatch."""
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    if state.get("version") != CHECKPOINT_VERSION:
+        raise ValueError("checkpoint version %r, expected %d" % (state.get("version"),
+                                                                CHECKPOINT_VERSION))
+    own = module.state_dict()
+    if set(own) != set(state["module"]) or any(own[k].shape != state["module"][k].shape
+                                               for k in own):
+        raise ValueError("checkpoint does not match the module's parameters")
+    module.load_state_dict(state["module"])
+    if opt is not None and "adam" in state:
+        a = state["adam"]
+        if len(a["m"]) != len(opt.m):
+            raise ValueError("checkpoint optimiser state does not match")
+        with torch.no_grad():
+            for dst, src in zip(opt.m + opt.v, a["m"] + a["v"]):
+                dst.copy_(src)
+        opt.step_count, opt.lr, opt.b1, opt.b2, opt.eps = (a["step_count"], a["lr"], a["b1"],
+                                                           a["b2"], a["eps"])
+    return state["step"], state["meta"]
+
+
 class Adam:
     """Adam over a list of parameters; the update runs in shl_nn_adam."""
 

@@ -29,6 +29,9 @@ HEADER = os.path.join(os.path.dirname(_build.PKG), "include", "shearlet.h")
 _lib = None
 
 
+SHL_ABI_VERSION_PY = 1   # the header's SHL_ABI_VERSION
+
+
 class ShearletError(RuntimeError):
     def __init__(self, fn, status, detail):
         super().__init__("%s failed: status %d (%s)" % (fn, status, detail))
@@ -326,6 +329,57 @@ class Bank:
         if self.general:
             d["spectra_imag"] = shl_bank_copy_spectra_imag(self.handle)
         return d
+
+    # ------------------------------------------------------- disk cache
+    @staticmethod
+    def cache_key(rows, cols, n_scales, shear_levels=None, full=False):
+        """Hex digest identifying a shearlet-system construction."""
+        import hashlib
+        lv = list(shear_levels) if shear_levels is not None else None
+        txt = "shl-bank-v1|%d|%d|%d|%s|%d|abi%d" % (rows, cols, n_scales, lv, int(bool(full)),
+                                                    SHL_ABI_VERSION_PY)
+        return hashlib.sha256(txt.encode()).hexdigest()[:24]
+
+    def save(self, path, key=""):
+        """Write the bank's float64 spectra (real and imaginary parts), indices
+        and cache key to ``path`` (.npz)."""
+        d = self.info()
+        imag = d.get("spectra_imag", np.zeros(0))
+        if not np.any(imag):
+            imag = np.zeros(0)          # a real bank stays real
+        np.savez(path, key=np.array(key), spectra=d["spectra"], imag=imag, idx=d["idx"],
+                 general=np.array(int(self.general)))
+
+    @classmethod
+    def load(cls, path, device=0, key=None):
+        """Bank from a file written by ``save``; with ``key`` given, the file's
+        key must match (else ValueError)."""
+        with np.load(path) as z:
+            if key is not None and str(z["key"]) != key:
+                raise ValueError("bank cache %s holds key %s, not %s" % (path, z["key"], key))
+            S, I, idx = z["spectra"], z["imag"], z["idx"]
+            general = bool(int(z["general"]))
+        if I.size:
+            return cls(shl_bank_create_general(S + 1j * I, idx, device), device)
+        if general:
+            return cls(shl_bank_create_general(S, idx, device), device)
+        return cls(shl_bank_create_from_spectra(S, idx, device), device)
+
+    @classmethod
+    def cached(cls, cache_dir, rows, cols, n_scales, shear_levels=None, full=False, device=0):
+        """``create`` through a directory of saved banks: load the file named by
+        the construction's key if present, else build, save and return."""
+        import os
+        key = cls.cache_key(rows, cols, n_scales, shear_levels, full)
+        path = os.path.join(cache_dir, "bank_%s.npz" % key)
+        if os.path.exists(path):
+            return cls.load(path, device, key)
+        b = cls.create(rows, cols, n_scales, shear_levels, full, device)
+        os.makedirs(cache_dir, exist_ok=True)
+        tmp = path + ".tmp.npz"
+        b.save(tmp, key)
+        os.replace(tmp, path)
+        return b
 
     def close(self):
         if self.handle is not None:
