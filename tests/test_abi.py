@@ -111,7 +111,7 @@ def test_host_only_bank_rejects_transform_calls(L):
     (64, 32, 2, [1, 2], True), (32, 32, 1, [0], False),
     # general sizes: float64 Bluestein line DFTs in the host builder
     (45, 60, 2, None, False), (33, 33, 1, None, True), (100, 72, 2, None, False),
-    (127, 128, 2, None, False), (7, 5, 1, None, False),
+    (127, 128, 2, None, False), (7, 5, 1, None, False), (35, 27, 2, [1, 2], True),
 ])
 def test_host_bank_builder_matches_oracle(rows, cols, J, levels, full):
     h = S.shl_bank_create(rows, cols, J, levels, full, device=-1)
