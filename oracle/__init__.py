@@ -22,6 +22,16 @@ apps
     Hard thresholding, PSNR, denoising (Sec. 4.2) and iterative hard
     thresholding inpainting (Alg. "Shearlet inpainting by iterative hard
     thresholding", Sec. 4.3).
+nn
+    The learned parts in float64 torch CPU ops: 3 x 3 convolution, PReLU,
+    pools, linear, softplus, the relaxed threshold, MSE, Adam, both networks,
+    the unrolled iteration (gradients by autograd).
+ray
+    The discrete parallel-beam ray transform of Sec. 4.4 (Joseph's method) as
+    an explicit sparse matrix, and exact line integrals of ellipses.
+lpd
+    The learned primal-dual reconstruction of Sec. 4.4 (Algorithm 2) in the
+    image and the shearlet domain.
 
 Every function computes in float64 / complex128.
 """
