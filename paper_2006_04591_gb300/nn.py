@@ -652,7 +652,7 @@ def save_checkpoint(path, module, opt=None, step=0, meta=None):
         state["adam"] = {"m": [m.cpu() for m in opt.m], "v": [v.cpu() for v in opt.v],
                          "step_count": opt.step_count, "lr": opt.lr, "b1": opt.b1,
                          "b2": opt.b2, "eps": opt.eps}
-    tmp = str(path) + ".tmp"
+    tmp = "%s.%d.tmp" % (path, os.getpid())
     torch.save(state, tmp)
     os.replace(tmp, path)
 

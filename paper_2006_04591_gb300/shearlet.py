@@ -376,9 +376,9 @@ class Bank:
             return cls.load(path, device, key)
         b = cls.create(rows, cols, n_scales, shear_levels, full, device)
         os.makedirs(cache_dir, exist_ok=True)
-        tmp = path + ".tmp.npz"
+        tmp = "%s.%d.tmp.npz" % (path, os.getpid())     # one writer per file name
         b.save(tmp, key)
-        os.replace(tmp, path)
+        os.replace(tmp, path)                           # atomic: readers see old or new
         return b
 
     def close(self):
