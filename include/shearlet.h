@@ -64,6 +64,11 @@ extern "C" {
 #endif
 
 #define SHL_ABI_VERSION 1
+/* Version of the filter-bank construction (host builder bank_build.cpp and
+ * GPU builder bank_gpu.cu, which produce the same spectra).  Raised whenever
+ * either changes its output; saved banks keyed on an older value are not
+ * reused. */
+#define SHL_BANK_BUILDER_VERSION 1
 
 typedef enum {
   SHL_OK = 0,
@@ -332,7 +337,10 @@ shl_status shl_profile_read(char* buf, size_t len);
  * if a kernel faulted, and SHL_ETIMEOUT if a bounded wait inside the
  * pipelined decomposition (between its column and row passes, Sec. 3.4)
  * ran out since the last shl_sync on this device; the coefficients of that
- * call are then incomplete.  The flag is per device and cleared on read. */
+ * call are then incomplete.  The flag is per device (the stream's device),
+ * is cleared only here, and while it is set every later pipelined
+ * decomposition on that device stops at once and leaves its coefficients
+ * incomplete: call shl_sync after such a call before the next one. */
 shl_status shl_sync(void* stream);
 
 #ifdef __cplusplus

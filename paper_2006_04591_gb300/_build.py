@@ -22,7 +22,7 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["fast.cu", "general.cu", "noalloc.cu", "nn.cu", "nn_tc.cu", "bank_gpu.cu", "ray.cu"]
+CU_SOURCES = ["fast.cu", "fused.cu", "general.cu", "noalloc.cu", "nn.cu", "nn_tc.cu", "bank_gpu.cu", "ray.cu"]
 CPP_SOURCES = ["api.cpp", "bank_build.cpp"]
 
 

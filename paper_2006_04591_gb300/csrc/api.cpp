@@ -165,9 +165,46 @@ bool use_pipe(const shl_bank* b) {
   return !b->general && pipe_cfg().on && shl::dec_pipe_supported(b->N, b->M);
 }
 
+// Paired-subband kernels (fused.cu): both passes of each direction in one
+// cluster launch, the plane between them in L2 instead of DRAM, for the
+// shapes pair_supported covers.  Opt-in with SHL_FUSED=1 (read once per
+// process): at 16 x 512 x 512, K = 49 they measured 0.67 + 0.83 ms against
+// 0.53 + 0.56 ms for the staged kernels, which run at higher issue
+// efficiency with two CTAs per SM.
+bool fused_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("SHL_FUSED");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+// Co-resident clusters of the paired kernels on the bank's device (0 when
+// the query fails, which keeps the staged kernels).
+int pair_ncl_max(const shl_bank* b) {
+  DevGuard g(b->device);
+  int n = 0;
+  if (shl::pair_max_clusters(b->N, &n) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return n;
+}
+bool use_pair(const shl_bank* b) {
+  return !b->general && b->device >= 0 && fused_on() && shl::pair_supported(b->N, b->M) &&
+         pair_ncl_max(b) > 0;
+}
+// Slot of one cluster: the complex plane of a subband pair, [M][N].
+size_t pair_slot_bytes(const shl_bank* b) { return (size_t)b->N * b->M * sizeof(float2); }
+
 size_t ws_need(const shl_bank* b, int batch, shl_op op) {
   const long long sub = (long long)batch * b->K;
   const size_t X = align256((size_t)batch * plane_bytes(b));
+  if ((op == SHL_OP_DECOMPOSE || op == SHL_OP_RECONSTRUCT) && use_pair(b)) {
+    const int ncl = pair_ncl_max(b);
+    const size_t slots = align256((size_t)ncl * pair_slot_bytes(b));
+    if (op == SHL_OP_DECOMPOSE) return X + slots;
+    return X + slots + align256((size_t)(ncl + batch - 1) * plane_bytes(b));
+  }
   if (op == SHL_OP_DECOMPOSE && use_pipe(b)) {
     const PipeCfg& c = pipe_cfg();
     const int nchunks = (int)((sub + c.CS - 1) / c.CS);
@@ -389,6 +426,18 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
   const float scale = (float)(1.0 / (double(N) * M));
   const float* invW = (flags & SHL_DUAL_WEIGHTED) ? b->dInvW : nullptr;
+  if (stage_override <= 0 && use_pair(b)) {
+    float2* slots = reinterpret_cast<float2*>(static_cast<char*>(ws) +
+                                              align256((size_t)batch * plane_bytes(b)));
+    const int ncl = shl::pair_clusters_for(pair_ncl_max(b), batch * ((K + 1) / 2));
+    {
+      Launch L_("pair_dec", st);
+      e = shl::launch_pair_dec(N, dtype == SHL_BF16, X, b->dG, invW, coeffs, slots, ncl, scale, K,
+                               batch, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "pair_dec");
+    return SHL_OK;
+  }
   if (stage_override <= 0 && use_pipe(b)) {
     const PipeCfg& c = pipe_cfg();
     unsigned* ctl = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(Z) +
@@ -458,6 +507,30 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
   const size_t esz = dtype == SHL_BF16 ? 2 : 4;
   const float scale = (float)(1.0 / (double(N) * M));
   cudaError_t e;
+  if (use_pair(b)) {
+    const int ncl_max = pair_ncl_max(b);
+    const int ncl = shl::pair_clusters_for(ncl_max, batch * ((K + 1) / 2));
+    float2* parts = reinterpret_cast<float2*>(reinterpret_cast<char*>(Z) +
+                                              align256((size_t)ncl_max * pair_slot_bytes(b)));
+    {
+      Launch L_("pair_rec", st);
+      e = shl::launch_pair_rec(N, dtype == SHL_BF16, coeffs, thresh, b->dG, Z, parts, ncl, K, batch,
+                               b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "pair_rec");
+    {
+      Launch L_("pair_final", st);
+      e = shl::launch_pair_final(N, parts, A, weights ? b->dInvW : nullptr, scale, K, batch, ncl,
+                                 b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "pair_final");
+    {
+      Launch L_("rows_c2r_image", st);
+      e = shl::launch_rows_c2r_t(M, false, A, x_out, N, batch, b->dTw, st);
+    }
+    if (e) return cuda_fail(e, "rows_c2r_image");
+    return SHL_OK;
+  }
   for (int s0 = 0; s0 < total;) {
     const int Sc = next_chunk(s0, total, S, K);
     {
@@ -1027,8 +1100,13 @@ shl_status shl_profile_read(char* buf, size_t len) {
 }
 
 shl_status shl_sync(void* stream) {
-  cudaError_t e = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
   if (e) return cuda_fail(e, "shl_sync");
+  // the wait flag lives on the stream's device: read and clear it there
+  int dev = -1;
+  if ((e = cudaStreamGetDevice(st, &dev))) return cuda_fail(e, "shl_sync");
+  DevGuard g(dev);
   unsigned flag = 0;
   if ((e = shl::read_pipe_error(&flag))) return cuda_fail(e, "shl_sync");
   if (flag)

@@ -60,6 +60,27 @@ __device__ __forceinline__ void cta_copy_async(void* dst, const void* src, int b
   for (int c = tid * 16; c < bytes; c += nthreads * 16) cp_async16(d + c, s + c);
 }
 
+// Split factor exp(-2 pi i p / M), p = j + u T, of the real-row transforms:
+// for M = 512 (T = 16 lanes) the lane base w0 = exp(-2 pi i j / 512) times
+// the 32nd root exp(-2 pi i u / 32) (u is a constant in the unrolled
+// loops); otherwise the staged table.
+template <int LOG_M, int T>
+__device__ __forceinline__ float2 split_tw(const float2* ptw, const float2* twb, int j, int u) {
+  if constexpr (LOG_M == 9 && T == 16) {
+    const float2 w0 = twb[4 * T + j];
+    switch (u) {
+#define SHL_SPLIT(U) case U: return rot32<U, -1>(w0);
+      SHL_SPLIT(0) SHL_SPLIT(1) SHL_SPLIT(2) SHL_SPLIT(3) SHL_SPLIT(4) SHL_SPLIT(5) SHL_SPLIT(6)
+      SHL_SPLIT(7) SHL_SPLIT(8) SHL_SPLIT(9) SHL_SPLIT(10) SHL_SPLIT(11) SHL_SPLIT(12)
+      SHL_SPLIT(13) SHL_SPLIT(14) SHL_SPLIT(15)
+#undef SHL_SPLIT
+      default: return ptw[j + u * T];
+    }
+  } else {
+    return ptw[j + u * T];
+  }
+}
+
 template <int LOG_M>
 struct RowsT {
   static constexpr int M = 1 << LOG_M;
@@ -79,7 +100,8 @@ struct RowsT {
   static constexpr size_t CSTAGE = sizeof(float2) * (size_t)Mh * CPITCH;
   static constexpr size_t SMEM_CAP = 224 * 1024;
   static constexpr int MINB = M <= 512 ? 2 : 1;    // CTAs per SM the sizes allow
-  static constexpr size_t TWB = sizeof(float2) * ((size_t)LineTw<L, R>::WORDS + L);  // twiddles
+  // twiddles: line stages, split factors exp(-2 pi i p / M), lane bases
+  static constexpr size_t TWB = sizeof(float2) * ((size_t)LineTw<L, R>::WORDS + L + LineTwB<L, R>::WORDS);
   static constexpr int CNST = 2 * CSTAGE + WORK + TWB <= SMEM_CAP ? 2 : 1;   // c2r pipeline depth
   static_assert(CSTAGE + WORK + TWB <= SMEM_CAP, "c2r tile does not fit shared memory");
 };
@@ -142,7 +164,8 @@ __device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], fl
                                                 int tid) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, TR = P::TR, TP = P::TP;
-  line_fft<L, R, -1>(v, line, j, 1 + r, twl);
+  const float2* twb = ptw + L;                             // lane bases after the split factors
+  line_fft_any<L, R, -1>(v, line, j, 1 + r, twl, twb);
 
   // conjugate-pair split needs Z[L - k]: publish the natural-order line
   group_sync<T>(1 + r);
@@ -156,7 +179,7 @@ __device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], fl
     const float2 A = v[u], B = mir[u];
     const float2 E = make_float2(0.5f * (A.x + B.x), 0.5f * (A.y - B.y));
     const float2 O = make_float2(0.5f * (A.y + B.y), -0.5f * (A.x - B.x));
-    v[u] = cadd(E, cmul(O, ptw[j + u * T]));
+    v[u] = cadd(E, cmul(O, split_tw<LOG_M, T>(ptw, twb, j, u)));
   }
   __syncthreads();                       // line buffers become the tile
   if (valid) {
@@ -196,6 +219,7 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
 
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
   if (NST == 2 && blockIdx.x < ntiles) r2c_issue<LOG_M, INM>(a, stages, blockIdx.x, tid);
   cp_async_commit();
   int k = 0;
@@ -292,10 +316,10 @@ __device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* lin
     const float2 B = tile[(L - kk) * CP + rr];
     const float2 S = make_float2(A.x + B.x, A.y - B.y);
     const float2 D = make_float2(A.x - B.x, A.y + B.y);
-    const float2 wd = cmulc(D, ptw[kk]);        // D * exp(+2 pi i k / M)
+    const float2 wd = cmulc(D, split_tw<LOG_M, T>(ptw, ptw + L, j, u));   // D * exp(+2 pi i k / M)
     v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
   }
-  line_fft<L, R, +1>(v, line, j, 1 + r, twl);
+  line_fft_any<L, R, +1>(v, line, j, 1 + r, twl, ptw + L);
 }
 
 // C2R of one staged tile and the store of row r to out + base.
@@ -342,6 +366,7 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
 
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
   if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M>(a, stages, blockIdx.x, tid);
   cp_async_commit();
   int k = 0;
@@ -394,6 +419,7 @@ k_rows_shrink_t(RowsShrinkArgs a) {
 
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
   if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M>(ca, stages, blockIdx.x, tid);
   cp_async_commit();
   int k = 0;
@@ -434,7 +460,7 @@ struct LinesT {
   static constexpr int THREADS = 256;
   static constexpr int NG = THREADS / T;              // lane groups per CTA
   static constexpr size_t SMEM_LINES = sizeof(float2) * (size_t)NG * C::WORDS;
-  static constexpr size_t TWB = sizeof(float2) * (size_t)LineTw<N, R>::WORDS;
+  static constexpr size_t TWB = sizeof(float2) * ((size_t)LineTw<N, R>::WORDS + LineTwB<N, R>::WORDS);
 };
 
 struct LinesArgs {
@@ -455,14 +481,16 @@ __global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
   const int g = threadIdx.x / T, j = threadIdx.x % T;
   float2* line = smem + (size_t)g * P::C::WORDS;
   float2* twl = smem + (size_t)P::NG * P::C::WORDS;
+  float2* twb = twl + LineTw<N, R>::WORDS;
   LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  LineTwB<N, R>::fill(twb, a.tw, threadIdx.x, P::THREADS);
   __syncthreads();
   for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
     float2* d = a.data + (size_t)q * N;
     float2 v[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) v[u] = d[j + u * T];
-    line_fft<N, R, -1>(v, line, j, 1 + g, twl);
+    line_fft_any<N, R, -1>(v, line, j, 1 + g, twl, twb);
 #pragma unroll
     for (int u = 0; u < R; ++u) d[j + u * T] = v[u];
   }
@@ -516,7 +544,7 @@ __device__ __forceinline__ void dec_group(const float2* X, float2* out, const fl
       if (W) gv *= __ldg(W + j + u * T);
       v[u] = cscale(Xl[u], gv);
     }
-    line_fft<N, R, +1>(v, line, j, 1 + g, twl);
+    line_fft_any<N, R, +1>(v, line, j, 1 + g, twl, twl + LineTw<N, R>::WORDS);
     float2* o = out + ((size_t)sl * Mh + kx) * N;
 #pragma unroll
     for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
@@ -532,6 +560,7 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   float2* line = smem + (size_t)g * P::C::WORDS;
   float2* twl = smem + (size_t)P::NG * P::C::WORDS;
   LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  LineTwB<N, R>::fill(twl + LineTw<N, R>::WORDS, a.tw, threadIdx.x, P::THREADS);
   __syncthreads();
   const int S = a.nlines / a.Mh;                        // subbands in the chunk
   const int ngroups = (S + DEC_FPG - 1) / DEC_FPG;
@@ -563,7 +592,9 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
   float2* twl = red + (size_t)NG * N;
   const int g = threadIdx.x / T, j = threadIdx.x % T;
   float2* line = smem + (size_t)g * P::C::WORDS;
+  float2* twb = twl + LineTw<N, R>::WORDS;
   LineTw<N, R>::fill(twl, a.tw, threadIdx.x, P::THREADS);
+  LineTwB<N, R>::fill(twb, a.tw, threadIdx.x, P::THREADS);
   __syncthreads();
   const int kx = blockIdx.x;
   const int b = a.b_lo + blockIdx.y;
@@ -593,7 +624,7 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
     group_sync<T>(1 + g);                   // line read before it is overwritten
     if (s + NG < s_end) fetch(s + NG);
     cp_async_commit();
-    line_fft<N, R, -1>(v, line, j, 1 + g, twl);
+    line_fft_any<N, R, -1>(v, line, j, 1 + g, twl, twb);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       const float gv = __ldg(G + j + u * T);
@@ -625,7 +656,7 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
     float2 v[R];
 #pragma unroll
     for (int u = 0; u < R; ++u) v[u] = red[j + u * T];
-    line_fft<N, R, +1>(v, line, j, 1, twl);
+    line_fft_any<N, R, +1>(v, line, j, 1, twl, twb);
 #pragma unroll
     for (int u = 0; u < R; ++u) A[j + u * T] = v[u];
   }
@@ -684,8 +715,8 @@ struct DecPipeT {
   static constexpr int MINB = (THREADS >= 512 || LOG_N >= 10) ? 1 : 2;
   // shared memory, float2 words: the role's twiddles, then its buffers
   // (ROW: two C2R stages + row line buffers; COL: column line buffers)
-  static constexpr size_t TWR = (size_t)LineTw<RP::L, RP::R>::WORDS + RP::L;
-  static constexpr size_t TWL = (size_t)LineTw<N, RL>::WORDS;
+  static constexpr size_t TWR = (size_t)LineTw<RP::L, RP::R>::WORDS + RP::L + LineTwB<RP::L, RP::R>::WORDS;
+  static constexpr size_t TWL = (size_t)LineTw<N, RL>::WORDS + LineTwB<N, RL>::WORDS;
   static constexpr size_t TW = TWR > TWL ? TWR : TWL;
   static constexpr size_t STW = RP::CSTAGE / sizeof(float2);
   static constexpr size_t ROWW = 2 * STW + (size_t)RP::LPC * RP::C::WORDS;
@@ -757,6 +788,7 @@ k_dec_pipe(DecPipeArgs a) {
   if ((int)blockIdx.x < a.ncol_ctas) {
     // ------------------------------------------------------------ COL role
     LineTw<N, RL>::fill(tws, a.tw, tid, P::THREADS);
+    LineTwB<N, RL>::fill(tws + LineTw<N, RL>::WORDS, a.tw, tid, P::THREADS);
     const int items = a.nchunks * NCOL;
     const int g = tid / TL, j = tid % TL;
     unsigned ahead = tid == 0 ? atomicAdd(a.ctl + 0, 1u) : 0u;   // one claim ahead
@@ -800,6 +832,7 @@ k_dec_pipe(DecPipeArgs a) {
   float2* rlines = area + 2 * P::STW;                  // row line buffers
   LineTw<L, RP::R>::fill(twr, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
+  LineTwB<L, RP::R>::fill(ptw + L, a.tw, tid, P::THREADS);
   const int ntiles = a.total * P::TPS;
   const unsigned need = (unsigned)NCOL + a.stall;      // COL items per chunk
   const int r = tid / TRow, j = tid % TRow;
@@ -1060,7 +1093,7 @@ cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ri
   a.nchunks = (total + CS - 1) / CS;
   // SHL_PIPE_STALL_TEST=1 (read per call): the ROW items wait for one COL
   // item more than exist, so every wait runs out; used to test that the
-  // bounded waits end the launch and shl_sync reports SHL_EDEVICE.
+  // bounded waits end the launch and shl_sync reports SHL_ETIMEOUT.
   const char* stall = std::getenv("SHL_PIPE_STALL_TEST");
   a.stall = (stall && stall[0] == '1') ? 1u : 0u;
   cudaError_t e = cudaMemsetAsync(ctl, 0, dec_pipe_ctl_bytes(a.nchunks), st);

@@ -49,6 +49,26 @@ cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ri
                             int CS, int NS, float col_frac, unsigned* ctl, const float2* tw,
                             cudaStream_t st);
 cudaError_t read_pipe_error(unsigned* flag);
+
+// Paired-subband kernels of fused.cu (square planes, see pair_supported):
+// one persistent cluster launch per direction, the plane between the passes
+// in a per-cluster slot of L * L * 8 bytes.
+bool pair_supported(int N, int M);
+// Co-resident clusters of the paired kernels on the current device.
+cudaError_t pair_max_clusters(int L, int* ncl);
+// Clusters a launch over `units` pairs uses.
+int pair_clusters_for(int ncl_max, int units);
+cudaError_t launch_pair_dec(int L, bool bf16, const float2* X, const float* G, const float* invW,
+                            void* coeffs, float2* slots, int ncl, float scale, int K, int B,
+                            const float2* tw, cudaStream_t st);
+// Writes the partial half planes [ncl + B - 1][Mh][L] of each image.
+cudaError_t launch_pair_rec(int L, bool bf16, const void* coeffs, const float* thresh,
+                            const float* G, float2* slots, float2* parts, int ncl, int K, int B,
+                            const float2* tw, cudaStream_t st);
+// Sums the partial planes of each image in cluster order, applies
+// scale [* 1/W] and the inverse column FFT into A [B][Mh][L].
+cudaError_t launch_pair_final(int L, const float2* parts, float2* A, const float* invW, float scale,
+                              int K, int B, int ncl, const float2* tw, cudaStream_t st);
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st);
 

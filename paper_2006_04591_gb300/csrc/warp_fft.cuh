@@ -165,6 +165,97 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], float2* sm, int j, int 
   }
 }
 
+// Per-lane twiddle bases of the 256- and 512-point lines (R = 16): for lane
+// j, [0..3] b, b^2, b^4, b^8 with b = exp(-2 pi i (j mod 16) / 256) (the
+// middle-stage twiddles b^u), [4] w0 = exp(-2 pi i j / 512) (the last stage
+// of the 512-point line, and with the 32nd roots of unity the real-FFT split
+// of a 512-point real row).  Stored [5][T], from the float64-built table.
+template <int L, int R>
+struct LineTwB {
+  static constexpr int T = L / R;
+  static constexpr bool OK = (L == 512 || L == 256) && R == 16;
+  static constexpr int WORDS = 5 * T;
+  static __device__ void fill(float2* sm, const float2* __restrict__ tw, int tid, int nthreads) {
+    for (int idx = tid; idx < WORDS; idx += nthreads) {
+      const int k = idx / T, j = idx - (idx / T) * T, m = j & 15;
+      sm[idx] = __ldg(tw + (k < 4 ? m * (16 << k) : j * 8));
+    }
+  }
+};
+
+// line_fft for the 256- and 512-point lines with the twiddles formed from
+// the lane's five bases (LineTwB) in registers: the same Stockham passes and
+// exchanges, 4 or 5 shared-memory loads per line instead of 15 or 23
+// (middle stage b^u: products of at most two bases; last stage of 512:
+// w0 times the 16th roots of unity).
+template <int L, int R, int SIGN>
+__device__ __forceinline__ void line_fft_b(float2 (&v)[R], float2* sm, int j, int bar_id,
+                                           const float2* __restrict__ twb) {
+  static_assert(LineTwB<L, R>::OK, "bases exist for 256 and 512 points, radix 16");
+  constexpr int T = L / R;
+  auto cj = [](float2 a) { return SIGN < 0 ? a : make_float2(a.x, -a.y); };
+  dft_reg<R, SIGN>(v);
+  group_sync<T>(bar_id);
+  {
+    float2* wp = sm + j * (R + 1);
+#pragma unroll
+    for (int u = 0; u < R; ++u) wp[u] = v[u];
+  }
+  group_sync<T>(bar_id);
+  const float2* rp = sm + pad_base<R>(j);
+#pragma unroll
+  for (int u = 0; u < R; ++u) v[u] = rp[u * (T + T / R)];
+  {
+    float2 w[R];
+    w[1] = cj(twb[j]); w[2] = cj(twb[T + j]); w[4] = cj(twb[2 * T + j]); w[8] = cj(twb[3 * T + j]);
+    w[3] = cmul(w[2], w[1]); w[5] = cmul(w[4], w[1]); w[6] = cmul(w[4], w[2]);
+    w[7] = cmul(w[4], w[3]); w[9] = cmul(w[8], w[1]); w[10] = cmul(w[8], w[2]);
+    w[11] = cmul(w[8], w[3]); w[12] = cmul(w[8], w[4]); w[13] = cmul(w[8], w[5]);
+    w[14] = cmul(w[8], w[6]); w[15] = cmul(w[8], w[7]);
+#pragma unroll
+    for (int u = 1; u < R; ++u) v[u] = cmul(v[u], w[u]);
+  }
+  dft_reg<R, SIGN>(v);
+  if constexpr (L == 512) {
+    group_sync<T>(bar_id);
+    {
+      float2* wp = sm + pad_base<R>(((j >> 4) << 8) + (j & 15));
+#pragma unroll
+      for (int u = 0; u < R; ++u) wp[u * (R + 1)] = v[u];
+    }
+    group_sync<T>(bar_id);
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = rp[u * (T + T / R)];
+    const float2 w0 = cj(twb[4 * T + j]);
+#pragma unroll
+    for (int q = 0; q < R / 2; ++q) {
+      float2 x1 = cmul(v[q + R / 2], w0);
+      switch (q) {            // times exp(SIGN 2 pi i q / 16)
+        case 1: x1 = rot32<2, SIGN>(x1); break;
+        case 2: x1 = rot32<4, SIGN>(x1); break;
+        case 3: x1 = rot32<6, SIGN>(x1); break;
+        case 4: x1 = rot32<8, SIGN>(x1); break;
+        case 5: x1 = rot32<10, SIGN>(x1); break;
+        case 6: x1 = rot32<12, SIGN>(x1); break;
+        case 7: x1 = rot32<14, SIGN>(x1); break;
+        default: break;
+      }
+      const float2 x0 = v[q];
+      v[q] = cadd(x0, x1);
+      v[q + R / 2] = csub(x0, x1);
+    }
+  }
+}
+
+// line_fft or, where the lane bases exist, line_fft_b.
+template <int L, int R, int SIGN>
+__device__ __forceinline__ void line_fft_any(float2 (&v)[R], float2* sm, int j, int bar_id,
+                                             const float2* __restrict__ stw_sm,
+                                             const float2* __restrict__ twb) {
+  if constexpr (LineTwB<L, R>::OK) line_fft_b<L, R, SIGN>(v, sm, j, bar_id, twb);
+  else line_fft<L, R, SIGN>(v, sm, j, bar_id, stw_sm);
+}
+
 // Store v[u] (natural positions j + u T) into the padded line buffer.
 template <int L, int R>
 __device__ __forceinline__ void line_store(const float2 (&v)[R], float2* sm, int j) {

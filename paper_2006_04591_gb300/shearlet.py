@@ -236,8 +236,53 @@ def shl_decompose(h, x, batch, coeffs, dtype, flags, ws, stream=None):
         _stream(stream, coeffs.device)))
 
 
+def bank_builder_version() -> int:
+    """SHL_BANK_BUILDER_VERSION as the header defines it (part of the bank
+    cache key, so that a changed construction never serves stale spectra)."""
+    m = re.search(r"#define\s+SHL_BANK_BUILDER_VERSION\s+(\d+)", open(HEADER).read())
+    if not m:
+        raise RuntimeError("SHL_BANK_BUILDER_VERSION not found in %s" % HEADER)
+    return int(m.group(1))
+
+
+def noalloc_scratch_bytes() -> int:
+    """SHL_NOALLOC_SCRATCH_BYTES as the header defines it."""
+    txt = open(HEADER).read()
+    m = re.search(r"#define\s+SHL_NOALLOC_SCRATCH_BYTES\s+\((\d+)u\s*<<\s*(\d+)\)", txt)
+    if not m:
+        raise RuntimeError("SHL_NOALLOC_SCRATCH_BYTES not found in %s" % HEADER)
+    return int(m.group(1)) << int(m.group(2))
+
+
+def noalloc_max_batch(rows, cols) -> int:
+    """Largest batch shl_decompose_noalloc accepts: the batch's image spectra
+    (rounded up to 256 bytes) plus one subband plane must fit the scratch."""
+    plane = rows * (cols // 2 + 1) * 8
+    cap = noalloc_scratch_bytes()
+    b = 0
+    while ((((b + 1) * plane + 255) // 256) * 256) + plane <= cap:
+        b += 1
+    return b
+
+
 def shl_decompose_noalloc(h, x, batch, coeffs, dtype, flags, stream=None):
-    """shl_decompose using the library's fixed scratch instead of a workspace."""
+    """shl_decompose using the library's fixed scratch instead of a workspace.
+
+    x and coeffs are checked against the bank's shape before the call: x
+    float32 with at least batch*rows*cols elements, coeffs of the element
+    type `dtype` names with at least batch*K*rows*cols elements, both on a
+    CUDA device."""
+    import torch
+    K, N, M = shl_bank_query(h)
+    want_dt = torch.float32 if dtype == SHL_F32 else torch.bfloat16 if dtype == SHL_BF16 else None
+    if want_dt is None:
+        raise ValueError("dtype must be SHL_F32 or SHL_BF16")
+    if not (x.is_cuda and coeffs.is_cuda):
+        raise ValueError("x and coeffs must be CUDA tensors")
+    if x.dtype != torch.float32 or not x.is_contiguous() or x.numel() < batch * N * M:
+        raise ValueError("x must be contiguous float32 with >= batch*rows*cols elements")
+    if coeffs.dtype != want_dt or not coeffs.is_contiguous() or coeffs.numel() < batch * K * N * M:
+        raise ValueError("coeffs must be contiguous %s with >= batch*K*rows*cols elements" % want_dt)
     _check("shl_decompose_noalloc", lib().shl_decompose_noalloc(
         h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _stream(stream, coeffs.device)))
 
@@ -336,8 +381,8 @@ class Bank:
         """Hex digest identifying a shearlet-system construction."""
         import hashlib
         lv = list(shear_levels) if shear_levels is not None else None
-        txt = "shl-bank-v1|%d|%d|%d|%s|%d|abi%d" % (rows, cols, n_scales, lv, int(bool(full)),
-                                                    SHL_ABI_VERSION_PY)
+        txt = "shl-bank-v1|%d|%d|%d|%s|%d|abi%d|builder%d" % (
+            rows, cols, n_scales, lv, int(bool(full)), SHL_ABI_VERSION_PY, bank_builder_version())
         return hashlib.sha256(txt.encode()).hexdigest()[:24]
 
     def save(self, path, key=""):
@@ -377,8 +422,12 @@ class Bank:
         b = cls.create(rows, cols, n_scales, shear_levels, full, device)
         os.makedirs(cache_dir, exist_ok=True)
         tmp = "%s.%d.tmp.npz" % (path, os.getpid())     # one writer per file name
-        b.save(tmp, key)
-        os.replace(tmp, path)                           # atomic: readers see old or new
+        try:
+            b.save(tmp, key)
+            os.replace(tmp, path)                       # atomic: readers see old or new
+        finally:
+            if os.path.exists(tmp):                     # save or replace failed
+                os.remove(tmp)
         return b
 
     def close(self):

@@ -242,11 +242,13 @@ def test_rows_of_512_decompose_f32_bf16_dual(rows, J, B):
 
 
 def test_chunking_does_not_change_results():
-    """One staging chunk (the default) and many small chunks (the fixed
-    scratch of shl_decompose_noalloc) run the same arithmetic: equal bits."""
+    """One staging chunk (the default of the staged kernels, which run the
+    512 x 256 planes) and many small chunks (the fixed scratch of
+    shl_decompose_noalloc: three chunks here) run the same arithmetic: equal
+    bits."""
     from paper_2006_04591_gb300 import shearlet as S
-    ref, bank = _bank(512, 512, 4)
-    x = torch.from_numpy(_images(4, 512, 512, 95)).cuda()
+    ref, bank = _bank(512, 256, 3)
+    x = torch.from_numpy(_images(4, 512, 256, 95)).cuda()
     a = bank.decompose(x)
     b = torch.empty_like(a)
     S.shl_decompose_noalloc(bank.handle, x, 4, b, S.SHL_F32, 0)

@@ -36,6 +36,23 @@ def test_bank_cache_round_trip(tmp_path):
     assert Bank.cache_key(32, 64, 2) != Bank.cache_key(32, 64, 2, [1, 2])
 
 
+def test_bank_cache_key_tracks_builder_and_cleans_up(tmp_path, monkeypatch):
+    """A changed builder version changes the key (no stale spectra), and a
+    save that fails leaves no temporary file in the cache directory."""
+    from paper_2006_04591_gb300 import shearlet as S
+    k1 = S.Bank.cache_key(32, 64, 2)
+    monkeypatch.setattr(S, "bank_builder_version", lambda: 10**6)
+    assert S.Bank.cache_key(32, 64, 2) != k1
+
+    def boom(self, path, key=""):
+        open(path, "wb").write(b"partial")
+        raise OSError("disk full")
+    monkeypatch.setattr(S.Bank, "save", boom)
+    with pytest.raises(OSError):
+        S.Bank.cached(str(tmp_path), 32, 64, 2, device=-1)
+    assert os.listdir(str(tmp_path)) == []
+
+
 def test_complex_bank_save_load(tmp_path):
     from paper_2006_04591_gb300.shearlet import Bank
     g = np.random.default_rng(0).standard_normal((3, 9, 7))
