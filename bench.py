@@ -93,6 +93,35 @@ def _profiled_traffic(kernel):
         return None
 
 
+def kernel_alg_bytes(name, B, K, N, M, s=4):
+    """Algorithmic HBM bytes one step's launches of kernel `name` move
+    (images, coefficients, filter and 1/W half spectra; no intermediates)."""
+    H = N * (M // 2 + 1)
+    img, coef, filt = B * N * M * 4, B * K * N * M * s, K * H * 4
+    return {
+        "rows_r2c_image": img, "rows_c2r_image": img, "lines_fwd_image": 0,
+        "dec_lines": filt, "rec_lines": filt + H * 4,
+        "rows_c2r_coeffs": coef, "rows_r2c_coeffs": coef,
+        "pair_dec": coef + filt, "pair_rec": coef + filt, "pair_final": H * 4,
+        "dec_pipe": coef + filt, "rows_shrink": 0,
+    }.get(name, 0)
+
+
+def roofline(prof, steps, B, K, N, M, s, peak, peak_src):
+    """Roofline of the kernel with the most device time in `prof` (the
+    library's per-launch CUDA-event profile over `steps` steps)."""
+    if not prof:
+        return None
+    name, rec = max(prof.items(), key=lambda kv: kv[1]["ms"])
+    per_launch_ms = rec["ms"] / rec["launches"]
+    per_step_launches = rec["launches"] / steps
+    alg = kernel_alg_bytes(name, B, K, N, M, s) / per_step_launches
+    achieved = alg / (per_launch_ms / 1e3) / 1e9
+    return {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": achieved / peak, "peak_source": peak_src, "launch_ms": per_launch_ms,
+            "algorithmic_bytes_per_launch": alg, "launches_per_step": per_step_launches}
+
+
 # ------------------------------------------------------- multi-rank logic
 def rank_seeds(rank: int, batch: int, base: int = 100):
     """Image seeds of one replica: each rank decomposes its own batch."""
@@ -164,7 +193,7 @@ class ClockSampler:
 _ORACLE_BANK = []
 
 
-def _oracle_sample(seconds_target=12.0, max_images=B_IMG):
+def _oracle_sample(seconds_target=12.0, max_images=B_IMG, first_seed=100):
     """Oracle dec+rec on whole images of the workload until ~seconds_target."""
     import numpy as np
     from oracle import bank as Bk
@@ -175,7 +204,7 @@ def _oracle_sample(seconds_target=12.0, max_images=B_IMG):
     ref = _ORACLE_BANK[0]
     done, t0 = 0, time.perf_counter()
     while done < max_images:
-        x = synth.cartoon(N_IMG, N_IMG, 100 + done).astype(np.float32)
+        x = synth.cartoon(N_IMG, N_IMG, first_seed + done).astype(np.float32)
         c = OT.decompose(x, ref["psi_hat"]).real
         OT.reconstruct(c, ref["psi_hat"])
         done += 1
@@ -243,27 +272,31 @@ def _cpu_cores_used():
 
 
 def run_reference(args):
+    """The FP64 oracle on the host: each step decomposes and reconstructs one
+    image of the workload (a bounded sample of the 16-image batch), and the
+    line reports exactly that: ms_per_step is the time of one such step and
+    value = K N^2 / that time, in the GPU arm's metric, unit and config."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     per_step = []
-    imgs = 0
     for s in range(args.warmup + args.steps):
-        n, dt = _oracle_sample(seconds_target=4.0, max_images=1)
+        n, dt = _oracle_sample(seconds_target=4.0, max_images=1, first_seed=100 + s % B_IMG)
         if s >= args.warmup:
             per_step.append(dt / n)
-            imgs += n
-    t_img = statistics.mean(per_step)
-    value = K_FILT * N_IMG * N_IMG / t_img
+    t_step = statistics.mean(per_step)
+    value = K_FILT * N_IMG * N_IMG / t_step
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_img * B_IMG * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": _config({"sample": "1 image (of 16) per step, dec+rec, K=49; "
-                                     "ms_per_step scaled to the 16-image batch"}),
+        "config": _config({"parallelism": "replicas" if int(os.environ.get("WORLD_SIZE", "1")) > 1
+                                          else "single"}),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": _cpu_cores_used(),
-                         "kind": "oracle", "sample": "%d images x K=49 dec+rec at 512^2" % imgs},
+                         "kind": "oracle",
+                         "sample": "one of the 16 images per step (dec+rec, K=49, 512^2, "
+                                   "FP64 numpy oracle); %d timed steps" % args.steps},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -375,6 +408,26 @@ def run_gpu(args):
     t_copy = reduce_max_time(sum(copy_times) / len(copy_times) / 1e3, dist if world > 1 else None, dev)
     if world > 1:
         dist.barrier()
+
+    # the same step with bfloat16-stored coefficients (RNE), its own roofline
+    c16 = torch.empty((B, K, N, N), dtype=torch.bfloat16, device=dev)
+
+    def step16():
+        bank.decompose(x, out=c16, ws=ws_d)
+        bank.reconstruct(c16, out=xr, ws=ws_r)
+
+    for _ in range(3):
+        step16()
+    torch.cuda.synchronize()
+    err16 = ((xr - x).abs().max() / x.abs().max()).item()
+    t16 = reduce_max_time(sum(timed(step16, args.steps)) / args.steps / 1e3,
+                          dist if world > 1 else None, dev)
+    S.shl_profile_enable(1)
+    S.shl_profile_read()
+    timed(step16, args.steps)
+    S.shl_profile_enable(0)
+    prof16 = S.shl_profile_read()
+    del c16
     clock_info = clocks.stop()
     clock_info["window"] = "timed, per-kernel-event and end-to-end passes"
 
@@ -390,30 +443,26 @@ def run_gpu(args):
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     # dominant kernel and its algorithmic bytes per launch
-    kern = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else (None, None)
-    roof = None
-    if kern[0] is not None:
-        name, rec = kern
-        per_launch_ms = rec["ms"] / rec["launches"]
-        per_step_launches = rec["launches"] / args.steps
-        per_kernel_bytes = {
-            "rows_c2r_coeffs": B * K * N * N * 4,     # coefficient stores of dec
-            "dec_pipe": B * K * N * N * 4 + K * (N // 2 + 1) * N * 4,   # + filters
-            "rows_r2c_coeffs": B * K * N * N * 4,     # coefficient loads of rec
-            "rows_r2c_image": B * N * N * 4,
-            "rows_c2r_image": B * N * N * 4,
-        }
-        step_bytes = per_kernel_bytes.get(name, 0)
-        alg = step_bytes / per_step_launches if per_step_launches else 0
-        achieved = alg / (per_launch_ms / 1e3) / 1e9
-        per_sub = _profiled_traffic(name)
-        traffic = per_sub * (B * K) / per_step_launches if per_sub is not None else None
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": hbm_peak,
-                "unit": "GB/s", "frac": achieved / hbm_peak, "traffic": traffic,
-                "peak_source": peak_src, "launch_ms": per_launch_ms,
-                "algorithmic_bytes_per_launch": alg}
+    roof = roofline(prof, args.steps, B, K, N, N, 4, hbm_peak, peak_src)
+    if roof is not None:
+        per_sub = _profiled_traffic(roof["kernel"])
+        roof["traffic"] = (per_sub * (B * K) / roof["launches_per_step"]
+                           if per_sub is not None else None)
 
     step_alg = dec_b + rec_b
+    dec16, rec16 = _algorithmic_bytes(B, K, N, N, s=2)
+    bf16_block = {
+        "coeff_dtype": "bf16 (RNE)", "ms_per_step": t16 * 1e3,
+        "value": job_value(B * K * N * N, world, t16), "unit": UNIT,
+        "vs_f32_time": t16 / t_step,
+        "step_hbm": {"algorithmic_bytes": dec16 + rec16,
+                     "achieved_gbs": (dec16 + rec16) / t16 / 1e9,
+                     "frac_of_peak": (dec16 + rec16) / t16 / 1e9 / hbm_peak},
+        "roofline": roofline(prof16, args.steps, B, K, N, N, 2, hbm_peak, peak_src),
+        "kernels": {k: {"launches_per_step": v["launches"] / args.steps,
+                        "ms_per_step": v["ms"] / args.steps} for k, v in prof16.items()},
+        "pr_rel_err": err16,
+    }
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True,
@@ -434,6 +483,7 @@ def run_gpu(args):
                 "max_rel_err": e2e_err,
                 "explicit_copies": {"value": coeffs_per_step / t_copy, "unit": UNIT,
                                     "transfer": "cudaMemcpyAsync H2D / D2H around the calls"}},
+        "bf16": bf16_block,
         "gpu_launches": launches,
         "clocks": clock_info,
         "pr_rel_err": err,

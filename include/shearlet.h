@@ -321,6 +321,22 @@ shl_status shl_subband_absmax(const shl_bank* bank, const void* coeffs, shl_dtyp
                               int batch, int by_rms, float* out, void* stream);
 
 /*
+ * shl_iht_thresholds - the threshold schedule of the inpainting iteration
+ * (Sec. 4.3, Alg. "Shearlet inpainting by iterative hard thresholding"), on
+ * the device so that no host read sits between the start value and the loop:
+ *   delta_0[b] = max_i absmax_by_rms[b][i]          (shl_subband_absmax, by_rms)
+ *   out[t][b][i] = delta_0[b] * lambda_b^t * RMS_i,  t = 0 .. iterations-1,
+ *   lambda_b = (delta_min / delta_0[b])^(1 / (iterations - 1))  (1 for one
+ *   iteration or delta_0 = 0), computed in float64 and rounded to float32.
+ * The printed decay delta_min^(1/(T-1)) reaches delta_min only for
+ * delta_0 = 1; the ratio above is that rule for any start value.
+ *   absmax_by_rms  device float32 [batch][K];  out  device float32
+ *   [iterations][batch][K].  delta_min > 0, else SHL_EINVAL.
+ */
+shl_status shl_iht_thresholds(const shl_bank* bank, const float* absmax_by_rms, int batch,
+                              int iterations, double delta_min, float* out, void* stream);
+
+/*
  * Launch accounting (no counterpart in the paper; instrumentation for
  * measurement).  shl_launch_count returns the number of kernels this
  * process's library calls have launched.  While shl_profile_enable(1) is in

@@ -47,8 +47,27 @@ def denoise(bank: Bank, x_noisy: torch.Tensor, sigma: float, factors=3.0,
 
 def iht_start_threshold(bank: Bank, f_masked: torch.Tensor, coeffs=None) -> torch.Tensor:
     """delta_init per image: max_{i,n} |c_i(n)| / RMS_i of SH f_masked ([B])."""
+    return iht_start_absmax(bank, f_masked, coeffs).amax(dim=1)
+
+
+def iht_start_absmax(bank: Bank, f_masked: torch.Tensor, coeffs=None) -> torch.Tensor:
+    """max_n |c_i(n)| / RMS_i of SH f_masked per (image, subband), [B, K] on the device."""
     c = bank.decompose(f_masked, out=coeffs)
-    return bank.subband_absmax(c, by_rms=True).amax(dim=1)
+    return bank.subband_absmax(c, by_rms=True)
+
+
+def iht_schedule(bank: Bank, f_masked: torch.Tensor, iterations: int, delta_min: float = 0.02,
+                 delta_init=None, coeffs=None) -> torch.Tensor:
+    """Thresholds delta_t RMS_i of every iteration, [T, B, K], formed on the
+    device (shl_iht_thresholds): no host read between the start value and
+    the loop.  delta_init None: max_{i,n} |c_i(n)| / RMS_i of SH f_masked."""
+    B = f_masked.shape[0]
+    if delta_init is None:
+        a = iht_start_absmax(bank, f_masked, coeffs)
+    else:
+        d = torch.as_tensor(delta_init, dtype=torch.float32).to(f_masked.device).reshape(-1)
+        a = d.expand(B).reshape(B, 1).expand(B, bank.K).contiguous()
+    return bank.iht_thresholds(a, iterations, delta_min)
 
 
 def iht_inpaint(bank: Bank, f_masked: torch.Tensor, mask: torch.Tensor, iterations: int,
@@ -67,18 +86,8 @@ def iht_inpaint(bank: Bank, f_masked: torch.Tensor, mask: torch.Tensor, iteratio
     coeffs = None
     if delta_init is None or not fused:
         coeffs = torch.empty((B, bank.K, bank.rows, bank.cols), dtype=coeff_dtype, device=dev)
-    if delta_init is None:
-        delta_init = iht_start_threshold(bank, f_masked, coeffs)
-    delta_init = torch.as_tensor(delta_init, dtype=torch.float64, device="cpu").reshape(-1)
-    if delta_init.numel() == 1:
-        delta_init = delta_init.expand(B)
-    d0 = delta_init.cpu().numpy().astype(np.float64)
     T = iterations
-    lam = (delta_min / d0) ** (1.0 / (T - 1)) if T > 1 else np.ones_like(d0)
-    rms = np.asarray(bank.rms, np.float64)
-    # thresholds of every iteration, [T, B, K], computed once
-    deltas = d0[None, :] * lam[None, :] ** np.arange(T)[:, None]
-    th = torch.from_numpy((deltas[:, :, None] * rms[None, None, :]).astype(np.float32)).to(dev)
+    th = iht_schedule(bank, f_masked, T, delta_min, delta_init, coeffs)   # [T, B, K], device
     f = torch.zeros_like(f_masked) if f_init is None else f_init.contiguous().float().clone()
     g = torch.empty_like(f)
     if fused:

@@ -1054,6 +1054,25 @@ shl_status shl_subband_absmax(const shl_bank* b, const void* coeffs, shl_dtype d
   return SHL_OK;
 }
 
+shl_status shl_iht_thresholds(const shl_bank* b, const float* absmax_by_rms, int batch,
+                              int iterations, double delta_min, float* out, void* stream) {
+  if (!b) return fail(SHL_EINVAL, "bank is NULL");
+  if (batch < 0 || iterations < 0) return fail(SHL_EINVAL, "batch and iterations must be >= 0");
+  if (batch == 0 || iterations == 0) return SHL_OK;
+  if (!(delta_min > 0.0)) return fail(SHL_EINVAL, "delta_min must be > 0");
+  if (b->device < 0) return fail(SHL_EINVAL, "bank was created host-only (device < 0)");
+  if (!absmax_by_rms || !out) return fail(SHL_EINVAL, "bad absmax / out pointer");
+  DevGuard g(b->device);
+  cudaError_t e;
+  {
+    Launch L_("iht_schedule", static_cast<cudaStream_t>(stream));
+    e = shl::launch_iht_schedule(absmax_by_rms, b->dRms, b->K, batch, iterations, delta_min, out,
+                                 static_cast<cudaStream_t>(stream));
+  }
+  if (e) return cuda_fail(e, "iht_schedule");
+  return SHL_OK;
+}
+
 long long shl_launch_count(void) { return g_launches.load(); }
 
 shl_status shl_profile_enable(int on) {

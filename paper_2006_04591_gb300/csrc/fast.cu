@@ -1140,6 +1140,41 @@ __global__ void __launch_bounds__(256) k_absmax(const void* coeffs, int K, size_
   }
 }
 
+// Iterative-hard-thresholding schedule (Sec. 4.3, Alg. inpainting): one CTA
+// per image; delta_0 = max_i a[b][i] (a = max |c_i| / RMS_i), then
+// th[t][b][i] = delta_0 lambda^t RMS_i, lambda = (delta_min / delta_0)^(1/(T-1)),
+// in float64 and rounded once.
+__global__ void __launch_bounds__(256) k_iht_schedule(const float* a, const float* rms, int K, int B,
+                                                      int T, double delta_min, float* th) {
+  const int b = blockIdx.x;
+  float m = 0.f;
+  for (int i = threadIdx.x; i < K; i += blockDim.x) m = fmaxf(m, a[(size_t)b * K + i]);
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ float red[8];
+  __shared__ double s_d0, s_lam;
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float r = red[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = fmaxf(r, red[w]);
+    s_d0 = (double)r;
+    s_lam = (T > 1 && r > 0.f) ? pow(delta_min / (double)r, 1.0 / (T - 1)) : 1.0;
+  }
+  __syncthreads();
+  const double d0 = s_d0, lam = s_lam;
+  for (int e = threadIdx.x; e < T * K; e += blockDim.x) {
+    const int t = e / K, i = e - t * K;
+    th[((size_t)t * B + b) * K + i] = (float)(d0 * pow(lam, (double)t) * (double)rms[i]);
+  }
+}
+
+cudaError_t launch_iht_schedule(const float* a, const float* rms, int K, int B, int T,
+                                double delta_min, float* th, cudaStream_t st) {
+  if (B == 0 || T == 0) return cudaSuccess;
+  k_iht_schedule<<<B, 256, 0, st>>>(a, rms, K, B, T, delta_min, th);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st) {
   if (nsub == 0) return cudaSuccess;

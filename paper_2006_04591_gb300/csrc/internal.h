@@ -71,6 +71,8 @@ cudaError_t launch_pair_final(int L, const float2* parts, float2* A, const float
                               int K, int B, int ncl, const float2* tw, cudaStream_t st);
 cudaError_t launch_absmax(const void* coeffs, bool bf16, int nsub, int K, size_t elems,
                           const float* rms, float* out, cudaStream_t st);
+cudaError_t launch_iht_schedule(const float* a, const float* rms, int K, int B, int T,
+                                double delta_min, float* th, cudaStream_t st);
 
 // Helpers of api.cpp used by noalloc.cu.
 shl_status set_error(shl_status s, const char* msg);

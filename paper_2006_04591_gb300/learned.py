@@ -173,14 +173,10 @@ def evaluate(bank: Bank, net, B=8, seed0=2000, plain_iters=60, delta_min=0.02, r
     fm = torch.from_numpy(masked.astype(np.float32)).to(dev)
     mk = torch.from_numpy(mask.astype(np.float32)).to(dev)
     mu8 = mk.to(torch.uint8)
-    rms = np.asarray(bank.rms, np.float64)
     stream = torch.cuda.current_stream(dev)
 
     def plain_thresholds():
-        d0 = apps.iht_start_threshold(bank, fm).double().cpu().numpy()
-        lam = (delta_min / d0) ** (1.0 / (plain_iters - 1))
-        deltas = d0[None, :] * lam[None, :] ** np.arange(plain_iters)[:, None]
-        return torch.from_numpy((deltas[:, :, None] * rms[None, None, :]).astype(np.float32)).to(dev)
+        return apps.iht_schedule(bank, fm, plain_iters, delta_min)
 
     # plain method: per-iteration PSNR (untimed pass) and per-iteration time (timed pass)
     psnr_plain = []
@@ -191,7 +187,7 @@ def evaluate(bank: Bank, net, B=8, seed0=2000, plain_iters=60, delta_min=0.02, r
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(plain_iters + 1)]
         torch.cuda.synchronize()
         evs[0].record(stream)
-        th = plain_thresholds()          # includes the start-threshold pass and its host read
+        th = plain_thresholds()          # includes the start-threshold decomposition
         hard_iht(bank, fm, mu8, th, out_each=lambda t, f: evs[t + 1].record(stream))
         torch.cuda.synchronize()
         t_plain.append([evs[0].elapsed_time(e) / 1e3 for e in evs[1:]])

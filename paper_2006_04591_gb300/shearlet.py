@@ -79,6 +79,7 @@ def lib():
         "shl_adjoint": (i, [vp, vp, i, i, vp, vp, vp, sz, vp]),
         "shl_shrink": (i, [vp, vp, vp, vp, i, vp, vp, vp, sz, vp]),
         "shl_subband_absmax": (i, [vp, vp, i, i, i, vp, vp]),
+        "shl_iht_thresholds": (i, [vp, vp, i, i, ctypes.c_double, vp, vp]),
         "shl_sync": (i, [vp]),
         "shl_launch_count": (ctypes.c_longlong, []),
         "shl_profile_enable": (i, [i]),
@@ -285,6 +286,13 @@ def shl_decompose_noalloc(h, x, batch, coeffs, dtype, flags, stream=None):
         raise ValueError("coeffs must be contiguous %s with >= batch*K*rows*cols elements" % want_dt)
     _check("shl_decompose_noalloc", lib().shl_decompose_noalloc(
         h, _ptr(x), batch, _ptr(coeffs), dtype, flags, _stream(stream, coeffs.device)))
+
+
+def shl_iht_thresholds(h, absmax_by_rms, batch, iterations, delta_min, out, stream=None):
+    """Inpainting threshold schedule [iterations][batch][K] on the device."""
+    _check("shl_iht_thresholds", lib().shl_iht_thresholds(
+        h, _ptr(absmax_by_rms), batch, iterations, float(delta_min), _ptr(out),
+        _stream(stream, out.device)))
 
 
 def shl_decompose_masked(h, f_masked, mask, f_est, batch, coeffs, dtype, ws, stream=None):
@@ -535,6 +543,15 @@ class Bank:
         ws = ws if ws is not None else self.workspace(SHL_OP_SHRINK, B)
         shl_shrink(self.handle, x, mask_u8, f_est, B, thresh, y, ws)
         return y
+
+    def iht_thresholds(self, absmax_by_rms, iterations, delta_min=0.02, out=None):
+        """[iterations, B, K] inpainting thresholds from max |c_i| / RMS_i [B, K]."""
+        import torch
+        B = absmax_by_rms.shape[0]
+        out = out if out is not None else torch.empty((iterations, B, self.K), dtype=torch.float32,
+                                                      device=absmax_by_rms.device)
+        shl_iht_thresholds(self.handle, absmax_by_rms.contiguous(), B, iterations, delta_min, out)
+        return out
 
     def subband_absmax(self, c, by_rms=False, out=None):
         import torch

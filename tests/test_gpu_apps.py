@@ -58,3 +58,31 @@ def test_iht_inpainting_matches_oracle(kind):
         p_gpu, p_ref = OA.psnr(clean[b], out[b]), OA.psnr(clean[b], want)
         assert abs(p_gpu - p_ref) < 0.05, (p_gpu, p_ref)
         assert p_gpu > OA.psnr(clean[b], masked[b]) + (8.0 if kind == "random" else 2.0)
+
+
+def test_iht_threshold_schedule_on_device():
+    """shl_iht_thresholds against the oracle's schedule delta_t RMS_i
+    (delta_0 = max |c_i| / RMS_i of SH f_masked, lambda reaching delta_min at
+    the last iteration): the same start value and decay, no host round trip."""
+    from paper_2006_04591_gb300 import apps
+    from paper_2006_04591_gb300.shearlet import Bank
+    N, T = 128, 12
+    ref = Bk.shearlet_bank(N, N, 3)
+    bank = Bank.from_spectra(ref["spectra"], ref["idx"], device=0)
+    clean, mask, masked = synth.inpaint_batch(3, N, 0.5, seed0=2100)
+    fm = torch.from_numpy(masked.astype(np.float32)).cuda()
+    th = apps.iht_schedule(bank, fm, T, 0.02).cpu().numpy()          # [T, B, K]
+    assert th.shape == (T, 3, bank.K)
+    for b in range(3):
+        _, hist, d0 = OA.iht_inpaint(masked[b].astype(np.float32).astype(np.float64), mask[b],
+                                     ref["psi_hat"], ref["rms"], T, 0.02, return_history=True)
+        want = hist[:, None] * ref["rms"][None, :]
+        np.testing.assert_allclose(th[:, b, :], want, rtol=2e-5)
+        np.testing.assert_allclose(th[-1, b, :], 0.02 * ref["rms"], rtol=2e-5)
+    # a given start value: the same schedule for every image; one iteration
+    th1 = apps.iht_schedule(bank, fm, 5, 0.1, delta_init=2.0).cpu().numpy()
+    lam = (0.1 / 2.0) ** 0.25
+    want1 = 2.0 * lam ** np.arange(5)[:, None, None] * ref["rms"][None, None, :]
+    np.testing.assert_allclose(th1, np.broadcast_to(want1, th1.shape), rtol=1e-6)
+    th0 = apps.iht_schedule(bank, fm, 1, 0.1, delta_init=3.0).cpu().numpy()
+    np.testing.assert_allclose(th0[0], np.broadcast_to(3.0 * ref["rms"], (3, bank.K)), rtol=1e-6)
