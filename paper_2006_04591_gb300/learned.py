@@ -263,11 +263,42 @@ def time_coeff_net_step(B=32, N=256, scales=3, steps=10, warmup=3, tc=True):
             "loss_first": losses[0], "loss_last": losses[-1]}
 
 
+CHECKPOINT_KIND = "threshold-net"
+
+
+def checkpoint_meta(bank: Bank, net, args=None):
+    """What a threshold-network checkpoint was trained for; load_threshold_net
+    refuses a checkpoint whose bank or iteration count differ."""
+    m = {"kind": CHECKPOINT_KIND, "size": bank.rows, "filters": bank.K, "iterations": int(net.T),
+         "pool": int(net.pool), "train_pairs": 2000, "train_seeds": "10000..11999",
+         "mask": "Bernoulli(0.5)"}
+    if args is not None:
+        m.update({"train_steps": args.steps, "train_batch": args.batch, "train_lr": args.lr})
+    return m
+
+
+def load_threshold_net(bank: Bank, path):
+    """ThresholdNet restored from a checkpoint written by ``main --save``."""
+    state = torch.load(path, map_location="cpu", weights_only=False)
+    meta = state.get("meta", {})
+    if meta.get("kind") != CHECKPOINT_KIND or meta.get("size") != bank.rows or \
+            meta.get("filters") != bank.K:
+        raise ValueError("checkpoint %s is not a threshold network for %d x %d, K = %d"
+                         % (path, bank.rows, bank.rows, bank.K))
+    net = nn.ThresholdNet(bank.K, T=int(meta["iterations"]), pool=int(meta.get("pool", 4)),
+                          device="cuda:%d" % bank.device)
+    nn.load_checkpoint(path, net)
+    return net
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--size", type=int, default=512)
     ap.add_argument("--steps", type=int, default=1500)
     ap.add_argument("--batch", type=int, default=4)
+    ap.add_argument("--iters", type=int, default=10, help="unrolled iterations T")
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--save", default=None, help="write the trained network (nn.save_checkpoint)")
     ap.add_argument("--out", default=None)
     ap.add_argument("--coeff-net", action="store_true", help="time the coefficient-network step")
     args = ap.parse_args()
@@ -282,11 +313,14 @@ def main():
         return
     bank = Bank.create(args.size, args.size, 4, device=0)
     t0 = time.time()
-    net, hist = train_thresholds(bank, steps=args.steps, batch=args.batch, log=print)
+    net, hist = train_thresholds(bank, steps=args.steps, batch=args.batch, T=args.iters,
+                                 lr=args.lr, log=print)
     train_s = time.time() - t0
     res = evaluate(bank, net)
     res.update({"train_steps": args.steps, "train_batch": args.batch, "train_pairs": 2000,
-                "train_seconds": train_s, "train_history": hist})
+                "train_lr": args.lr, "train_seconds": train_s, "train_history": hist})
+    if args.save:
+        nn.save_checkpoint(args.save, net, step=args.steps, meta=checkpoint_meta(bank, net, args))
     print(json.dumps({k: v for k, v in res.items() if k != "plain_psnr_per_iteration"}))
     if args.out:
         with open(args.out, "w") as fh:

@@ -167,12 +167,31 @@ def ssim(x, ref, data_range=1.0):
 
 
 # ---------------------------------------------------------------- training
+def resume_meta(checkpoint, domain, N, A, scales):
+    """Metadata of an existing checkpoint that may be resumed by a run with
+    these settings; ValueError if it was written for another network."""
+    meta = torch.load(checkpoint, map_location="cpu", weights_only=False).get("meta", {})
+    want = {"domain": domain, "size": N, "angles": A, "scales": scales}
+    got = {k: meta.get(k) for k in want}
+    if got != want:
+        raise ValueError("checkpoint %s was written for %s, not %s" % (checkpoint, got, want))
+    return meta
+
+
+def cosine_lr(lr, it, sched_steps):
+    """Cosine decay of the learning rate over sched_steps (held at the end)."""
+    return 0.5 * lr * (1.0 + math.cos(math.pi * min(it, sched_steps) / sched_steps))
+
+
 def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=0, scales=2,
-          log_every=100, checkpoint=None):
+          log_every=100, checkpoint=None, ckpt_every=500):
     """Train the ``domain`` network for ``steps`` steps.  With ``checkpoint``
-    (a file path) an existing checkpoint is resumed (parameters, Adam state,
-    step; the data stream restarts at that step's seeds) and the final state
-    is written there."""
+    (a file path) the state is written there every ``ckpt_every`` steps and
+    at the end (atomically), and an existing checkpoint is resumed:
+    parameters, Adam state and step, with its learning-rate schedule (total
+    steps and rate) kept, while the data stream restarts at that step's
+    seeds.  A checkpoint of another domain, size, angle count or scale count
+    is refused (ValueError)."""
     op = RayTransform(N, A, device=0)
     bank = Bank.create(N, N, scales, device=0) if domain == "shearlet" else None
     net = LPD(op, domain, bank, seed=seed)
@@ -182,13 +201,17 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
     gen = torch.Generator(device="cuda").manual_seed(seed + 7)
     rng = np.random.default_rng(seed)
     hist, t_steps = [], []
-    start = 0
+    start, sched_steps, base_lr = 0, steps, lr
     if checkpoint is not None and os.path.exists(checkpoint):
+        meta = resume_meta(checkpoint, domain, N, A, scales)
         start, _ = NN.load_checkpoint(checkpoint, net, opt)
+        sched_steps, base_lr = int(meta.get("steps", steps)), float(meta.get("lr", lr))
         rng = np.random.default_rng([seed, start])
         gen = torch.Generator(device="cuda").manual_seed(seed + 7 + 1000003 * start)
+    meta = {"domain": domain, "size": N, "angles": A, "scales": scales, "batch": batch,
+            "n_train": n_train, "seed": seed, "steps": sched_steps, "lr": base_lr}
     for it in range(start, steps):
-        opt.lr = 0.5 * lr * (1.0 + math.cos(math.pi * it / steps))
+        opt.lr = cosine_lr(base_lr, it, sched_steps)
         idx = torch.from_numpy(rng.integers(0, n_train, batch)).cuda()
         f_true = pool[idx].contiguous()
         g = noisy_data(op, f_true, gen)
@@ -203,9 +226,10 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
         t_steps.append(time.perf_counter() - t0)
         if it % log_every == 0 or it == steps - 1:
             hist.append((it, float(loss.item())))
+        if checkpoint is not None and ckpt_every > 0 and (it + 1) % ckpt_every == 0:
+            NN.save_checkpoint(checkpoint, net, opt, step=it + 1, meta=meta)
     if checkpoint is not None:
-        NN.save_checkpoint(checkpoint, net, opt, step=steps,
-                           meta={"domain": domain, "size": N, "angles": A, "scales": scales})
+        NN.save_checkpoint(checkpoint, net, opt, step=max(steps, start), meta=meta)
     return net, op, bank, hist, t_steps
 
 

@@ -90,3 +90,23 @@ def test_checkpoint_round_trip(tmp_path):
     torch.save(st, p)
     with pytest.raises(ValueError):
         nn.load_checkpoint(p, net2)
+
+
+def test_lpd_resume_checks_the_run_and_keeps_the_schedule(tmp_path):
+    """A learned primal-dual checkpoint is resumed only by a run of the same
+    domain, size, angle and scale counts; the cosine schedule is the one the
+    checkpoint records (held at its end when a run asks for more steps)."""
+    from paper_2006_04591_gb300 import lpd, nn
+    net = nn.CoeffNet(3, ch=4, seed=0, device="cpu", tc=False)
+    p = str(tmp_path / "lpd.pt")
+    meta = {"domain": "shearlet", "size": 128, "angles": 30, "scales": 2, "steps": 400, "lr": 1e-3}
+    nn.save_checkpoint(p, net, step=200, meta=meta)
+    assert lpd.resume_meta(p, "shearlet", 128, 30, 2)["steps"] == 400
+    for bad in (("image", 128, 30, 2), ("shearlet", 64, 30, 2), ("shearlet", 128, 60, 2),
+                ("shearlet", 128, 30, 3)):
+        with pytest.raises(ValueError):
+            lpd.resume_meta(p, *bad)
+    assert lpd.cosine_lr(1e-3, 0, 400) == pytest.approx(1e-3)
+    assert lpd.cosine_lr(1e-3, 200, 400) == pytest.approx(0.5e-3)
+    assert lpd.cosine_lr(1e-3, 400, 400) == pytest.approx(0.0, abs=1e-12)
+    assert lpd.cosine_lr(1e-3, 900, 400) == pytest.approx(0.0, abs=1e-12)
