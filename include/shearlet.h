@@ -359,6 +359,20 @@ shl_status shl_profile_read(char* buf, size_t len);
  * incomplete: call shl_sync after such a call before the next one. */
 shl_status shl_sync(void* stream);
 
+/*
+ * Checked build (a build step, not the paper's method): libshearlet_checked.so
+ * is the same library compiled with -DSHL_CHECKED, in which every global
+ * access of the power-of-two transform kernels first compares its index with
+ * the extent of its buffer as the launch's sizes give it.  An index outside
+ * sets a bit of a per-device guard word and the access is skipped, so an
+ * indexing error shows up here instead of as a fault.
+ *   shl_checked_build  1 in the checked library, 0 in libshearlet.so.
+ *   shl_check_status   synchronises `device`, then reads and clears its
+ *                      guard word into *word (always 0 in libshearlet.so).
+ */
+int shl_checked_build(void);
+shl_status shl_check_status(int device, unsigned* word);
+
 #ifdef __cplusplus
 }
 #endif

@@ -455,7 +455,7 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
     const int Sc = std::min(S, total - s0);
     {
       Launch L_("dec_lines", st);
-      e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
     }
     if (e) return cuda_fail(e, "dec_lines");
     {
@@ -545,7 +545,7 @@ shl_status reconstruct_impl(const shl_bank* b, const void* coeffs, shl_dtype dty
     {
       Launch L_("rec_lines", st);
       e = shl::launch_rec_lines(N, Z, A, b->dG, weights ? b->dInvW : nullptr, scale, Mh, K, s0,
-                                Sc, b->dTw, st);
+                                Sc, b->dTw, st, batch);
     }
     if (e) return cuda_fail(e, "rec_lines");
     s0 += Sc;
@@ -605,7 +605,8 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
     const int Sc = next_chunk(s0, total, S, K);
     {
       Launch L_("dec_lines", st);
-      e = shl::launch_dec_lines(N, X, Z, b->dG, nullptr, scale, Mh, K, s0, Sc, b->dTw, st);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, nullptr, scale, Mh, K, s0, Sc, b->dTw, st,
+                                   batch);
     }
     if (e) return cuda_fail(e, "dec_lines");
     {
@@ -615,7 +616,8 @@ shl_status shrink_impl(const shl_bank* b, const float* x, const unsigned char* m
     if (e) return cuda_fail(e, "rows_shrink");
     {
       Launch L_("rec_lines", st);
-      e = shl::launch_rec_lines(N, Z, A, b->dG, b->dInvW, scale, Mh, K, s0, Sc, b->dTw, st);
+      e = shl::launch_rec_lines(N, Z, A, b->dG, b->dInvW, scale, Mh, K, s0, Sc, b->dTw, st,
+                                  batch);
     }
     if (e) return cuda_fail(e, "rec_lines");
     s0 += Sc;
@@ -1116,6 +1118,23 @@ shl_status shl_profile_read(char* buf, size_t len) {
   if (err != cudaSuccess) return cuda_fail(err, "shl_profile_read");
   if (js.size() + 1 > len) return fail(SHL_EINVAL, "buffer too small for the profile summary");
   return SHL_OK;
+}
+
+shl_status shl_check_status(int device, unsigned* word) {
+  if (!word) return fail(SHL_EINVAL, "word is NULL");
+  DevGuard g(device);
+  cudaError_t e = cudaDeviceSynchronize();
+  if (!e) e = shl::read_check_word(word);
+  if (e) return cuda_fail(e, "shl_check_status");
+  return SHL_OK;
+}
+
+int shl_checked_build(void) {
+#ifdef SHL_CHECKED
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 shl_status shl_sync(void* stream) {

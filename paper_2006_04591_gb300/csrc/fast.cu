@@ -35,7 +35,10 @@
 #include <cmath>
 #include <cstdlib>
 
+#include "check.cuh"
 #include "warp_fft.cuh"
+
+SHL_CHECK_WORD_DEFINE
 
 namespace shl {
 
@@ -142,6 +145,7 @@ __device__ __forceinline__ void r2c_issue(const RowsTArgs& a, char* stage, int t
   const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
   const size_t row0 = (size_t)s * a.N + y0;
   constexpr int n = P::TR * P::M;
+  if (!SHL_IN(row0 + P::TR - 1, (size_t)a.nsub * a.N, CHK_R2C_IN)) return;
   if constexpr (INM == IN_MASKED) {
     cta_copy_async(stage, static_cast<const float*>(a.in) + row0 * P::M, n * 4, tid, P::THREADS);
     cta_copy_async(stage + n * 4, a.fest + row0 * P::M, n * 4, tid, P::THREADS);
@@ -161,7 +165,7 @@ template <int LOG_M>
 __device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], float2* line,
                                                 float2* tile, const float2* twl, const float2* ptw,
                                                 float2* out, int N, int r, int j, bool valid,
-                                                int tid) {
+                                                int tid, bool store_ok = true) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, TR = P::TR, TP = P::TP;
   const float2* twb = ptw + L;                             // lane bases after the split factors
@@ -192,7 +196,8 @@ __device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], fl
   for (int idx = tid; idx < Mh * (TR / 2); idx += P::THREADS) {
     const int kx = idx / (TR / 2), q = 2 * (idx % (TR / 2));
     const float2 lo = tile[kx * TP + q], hi = tile[kx * TP + q + 1];
-    *reinterpret_cast<float4*>(out + (size_t)kx * N + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
+    if (store_ok)
+      *reinterpret_cast<float4*>(out + (size_t)kx * N + q) = make_float4(lo.x, lo.y, hi.x, hi.y);
   }
   __syncthreads();
 }
@@ -246,8 +251,9 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     const uchar2* src_m = NST > 0 ? reinterpret_cast<const uchar2*>(cur + n * 8)
                                   : reinterpret_cast<const uchar2*>(a.mask ? a.mask + grow0 : nullptr);
     float tau = 0.f;
-    if (THRESH) tau = __ldg(a.thresh + s);
+    if (THRESH) tau = SHL_IN(s, a.nsub, CHK_R2C_IN) ? __ldg(a.thresh + s) : 0.f;
     const int rr = valid ? r : 0;
+    const bool tile_ok = SHL_IN((size_t)s * a.N + y0 + TR - 1, (size_t)a.nsub * a.N, CHK_R2C_OUT);
 
     float2 v[R];
 #pragma unroll
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     }
 
     r2c_tile_finish<LOG_M>(v, line, tile, twl, ptw, a.out + (size_t)s * Mh * a.N + y0, a.N, r, j,
-                           valid, tid);    // ends with a barrier: tile and stage reusable
+                           valid, tid, tile_ok);    // ends with a barrier: tile and stage reusable
   }
   cp_async_wait0();
 }
@@ -292,6 +298,7 @@ __device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, 
   const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
   const float2* in = a.in + (size_t)s * P::Mh * a.N + y0;
   constexpr int CH = P::TR / 2;                       // 16-byte chunks per kx row
+  if (!SHL_IN((size_t)s * a.N + y0 + P::TR - 1, (size_t)a.nsub * a.N, CHK_C2R_IN)) return;
   for (int c = tid; c < P::Mh * CH; c += P::THREADS) {
     const int kx = c / CH, q = c % CH;
     cp_async16(stage + kx * P::CPITCH + 2 * q, in + (size_t)kx * a.N + 2 * q);
@@ -380,7 +387,8 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
 
     c2r_tile_body<LOG_M, BF16OUT>(tile, line, twl, ptw, a.out, ((size_t)s * a.N + y0 + rr) * P::M, r,
-                                  j, valid);
+                                  j, valid && SHL_IN((size_t)s * a.N + y0 + rr, (size_t)a.nsub * a.N,
+                                                     CHK_C2R_OUT));
     __syncthreads();                       // stage reuse
   }
   cp_async_wait0();
@@ -432,7 +440,7 @@ k_rows_shrink_t(RowsShrinkArgs a) {
     const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
     float2 v[R];
     c2r_tile_compute<LOG_M>(stages + (k % NST) * SW, line, twl, ptw, r, j, valid, v);
-    const float tau = __ldg(a.thresh + s);
+    const float tau = SHL_IN(s, a.nsub, CHK_SHRINK) ? __ldg(a.thresh + s) : 0.f;
 #pragma unroll
     for (int u = 0; u < R; ++u) {
       if (fabsf(v[u].x) < tau) v[u].x = 0.f;
@@ -471,6 +479,7 @@ struct LinesArgs {
   const float2* tw;
   float scale;
   int Mh, K, s0, nlines;
+  int nimg;                  // image planes of data (checked build)
 };
 
 template <int LOG_N>
@@ -486,6 +495,7 @@ __global__ void __launch_bounds__(256) k_lines_fwd(LinesArgs a) {
   LineTwB<N, R>::fill(twb, a.tw, threadIdx.x, P::THREADS);
   __syncthreads();
   for (int q = blockIdx.x * P::NG + g; q < a.nlines; q += gridDim.x * P::NG) {
+    if (!SHL_IN(q, a.nlines, CHK_LINES)) break;
     float2* d = a.data + (size_t)q * N;
     float2 v[R];
 #pragma unroll
@@ -507,7 +517,8 @@ template <int LOG_N>
 __device__ __forceinline__ void dec_group(const float2* X, float2* out, const float* Gall,
                                           const float* invW, float scale, int Mh, int K, int s0,
                                           int sl0, int sl1, int kx, float2* line, const float2* twl,
-                                          int j, int g) {
+                                          int j, int g, int nimg = 0x7fffffff,
+                                          int nstage = 0x7fffffff) {
   using P = LinesT<LOG_N>;
   constexpr int T = P::T, R = P::R, N = P::N;
   const float* W = invW ? invW + (size_t)kx * N : nullptr;
@@ -517,15 +528,17 @@ __device__ __forceinline__ void dec_group(const float2* X, float2* out, const fl
   {
     const int s = s0 + sl0, b = s / K, i = s - b * K;
     const float* G = Gall + ((size_t)i * Mh + kx) * N;
+    const bool ok = SHL_IN((size_t)i * Mh + kx, (size_t)K * Mh, CHK_DEC_G);
 #pragma unroll
-    for (int u = 0; u < R; ++u) gn[u] = __ldg(G + j + u * T);
+    for (int u = 0; u < R; ++u) gn[u] = ok ? __ldg(G + j + u * T) : 0.f;
   }
   for (int sl = sl0; sl < sl1; ++sl) {
     const int s = s0 + sl, b = s / K;
     if (b != b_loaded) {                              // image spectrum line, once per image
       const float2* Xp = X + ((size_t)b * Mh + kx) * N;
+      const bool ok = SHL_IN((size_t)b * Mh + kx, (size_t)nimg * Mh, CHK_DEC_X);
 #pragma unroll
-      for (int u = 0; u < R; ++u) Xl[u] = Xp[j + u * T];
+      for (int u = 0; u < R; ++u) Xl[u] = ok ? Xp[j + u * T] : make_float2(0.f, 0.f);
       b_loaded = b;
     }
     float gc[R];
@@ -534,8 +547,9 @@ __device__ __forceinline__ void dec_group(const float2* X, float2* out, const fl
     if (sl + 1 < sl1) {                               // prefetch the next filter's line
       const int s2 = s + 1, i2 = s2 - (s2 / K) * K;
       const float* G2 = Gall + ((size_t)i2 * Mh + kx) * N;
+      const bool ok = SHL_IN((size_t)i2 * Mh + kx, (size_t)K * Mh, CHK_DEC_G);
 #pragma unroll
-      for (int u = 0; u < R; ++u) gn[u] = __ldg(G2 + j + u * T);
+      for (int u = 0; u < R; ++u) gn[u] = ok ? __ldg(G2 + j + u * T) : 0.f;
     }
     float2 v[R];
 #pragma unroll
@@ -546,8 +560,10 @@ __device__ __forceinline__ void dec_group(const float2* X, float2* out, const fl
     }
     line_fft_any<N, R, +1>(v, line, j, 1 + g, twl, twl + LineTw<N, R>::WORDS);
     float2* o = out + ((size_t)sl * Mh + kx) * N;
+    if (SHL_IN((size_t)sl * Mh + kx, (size_t)nstage * Mh, CHK_DEC_OUT)) {
 #pragma unroll
-    for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
+      for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
+    }
   }
 }
 
@@ -569,7 +585,7 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
     const int m = q / a.Mh, kx = q - m * a.Mh;
     const int sl0 = m * DEC_FPG, sl1 = min(S, sl0 + DEC_FPG);
     dec_group<LOG_N>(a.data, a.out, a.G, a.invW, a.scale, a.Mh, a.K, a.s0, sl0, sl1, kx, line, twl,
-                     j, g);
+                     j, g, a.nimg, S);
   }
 }
 
@@ -581,6 +597,7 @@ struct RecLinesArgs {
   const float2* tw;
   float scale;
   int Mh, K, s0, Sc, b_lo;
+  int nimg;                  // image planes of acc (checked build)
 };
 
 template <int LOG_N>
@@ -610,12 +627,14 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
   float2* pre = red + (size_t)g * N;
   auto fetch = [&](int s) {
     const float2* U = a.stage + ((size_t)(s - a.s0) * a.Mh + kx) * N;
+    if (!SHL_IN((size_t)(s - a.s0) * a.Mh + kx, (size_t)a.Sc * a.Mh, CHK_REC_STAGE)) return;
     for (int c = j; c < N / 2; c += T) cp_async16(pre + 2 * c, U + 2 * c);
   };
   if (s_begin + g < s_end) fetch(s_begin + g);
   cp_async_commit();
   for (int s = s_begin + g; s < s_end; s += NG) {
     const float* G = a.G + ((size_t)(s - b * a.K) * a.Mh + kx) * N;
+    const bool gok = SHL_IN((size_t)(s - b * a.K) * a.Mh + kx, (size_t)a.K * a.Mh, CHK_REC_G);
     cp_async_wait0();                       // this lane's copies of line s
     group_sync<T>(1 + g);                   // ... and the whole group's
     float2 v[R];
@@ -627,7 +646,7 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
     line_fft_any<N, R, -1>(v, line, j, 1 + g, twl, twb);
 #pragma unroll
     for (int u = 0; u < R; ++u) {
-      const float gv = __ldg(G + j + u * T);
+      const float gv = gok ? __ldg(G + j + u * T) : 0.f;
       acc[u].x = fmaf(gv, v[u].x, acc[u].x);
       acc[u].y = fmaf(gv, v[u].y, acc[u].y);
     }
@@ -638,6 +657,7 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
   for (int u = 0; u < R; ++u) red[(size_t)g * N + j + u * T] = acc[u];
   __syncthreads();
   float2* A = a.acc + ((size_t)b * a.Mh + kx) * N;
+  if (!SHL_IN((size_t)b * a.Mh + kx, (size_t)a.nimg * a.Mh, CHK_REC_ACC)) A = red + (size_t)(NG - 1) * N;
   for (int p = threadIdx.x; p < N; p += P::THREADS) {
     float2 sum = red[p];
     for (int q = 1; q < NG; ++q) sum = cadd(sum, red[(size_t)q * N + p]);
@@ -1030,10 +1050,10 @@ cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, 
 
 cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
                              float scale, int Mh, int K, int s0, int S, const float2* tw,
-                             cudaStream_t st) {
+                             cudaStream_t st, int nimg) {
   LinesArgs a{};
   a.data = const_cast<float2*>(X); a.out = out; a.G = G; a.invW = invW; a.tw = tw;
-  a.scale = scale; a.Mh = Mh; a.K = K; a.s0 = s0; a.nlines = S * Mh;
+  a.scale = scale; a.Mh = Mh; a.K = K; a.s0 = s0; a.nlines = S * Mh; a.nimg = nimg;
   RecLinesArgs ra{};
 #define CALL(X) lines_t<X>(1, a, ra, 0, st)
   SHL_SWITCH_LOG(ilog2(N), CALL)
@@ -1042,9 +1062,9 @@ cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G
 
 cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
-                             const float2* tw, cudaStream_t st) {
+                             const float2* tw, cudaStream_t st, int nimg) {
   LinesArgs a{};
-  RecLinesArgs ra{stage, acc, G, invW, tw, scale, Mh, K, s0, Sc, s0 / K};
+  RecLinesArgs ra{stage, acc, G, invW, tw, scale, Mh, K, s0, Sc, s0 / K, nimg};
   const int b_hi = (s0 + Sc - 1) / K;
   const int gy = Sc > 0 ? b_hi - ra.b_lo + 1 : 0;
   if (gy == 0) return cudaSuccess;
@@ -1106,6 +1126,22 @@ cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ri
   return cudaErrorInvalidValue;
 }
 
+// Reads and clears the checked build's guard word of the current device
+// (always 0 without SHL_CHECKED).
+cudaError_t read_check_word(unsigned* word) {
+#ifdef SHL_CHECKED
+  cudaError_t e = cudaMemcpyFromSymbol(word, g_shl_check, sizeof(unsigned));
+  if (e == cudaSuccess && *word) {
+    const unsigned zero = 0;
+    e = cudaMemcpyToSymbol(g_shl_check, &zero, sizeof(unsigned));
+  }
+  return e;
+#else
+  *word = 0;
+  return cudaSuccess;
+#endif
+}
+
 // Reads and clears the pipelined-wait error flag of the current device.
 cudaError_t read_pipe_error(unsigned* flag) {
   cudaError_t e = cudaMemcpyFromSymbol(flag, g_pipe_err, sizeof(unsigned));
@@ -1122,6 +1158,7 @@ __global__ void __launch_bounds__(256) k_absmax(const void* coeffs, int K, size_
                                                 const float* rms, float* out) {
   const int s = blockIdx.x;
   float m = 0.f;
+  if (!SHL_IN(s % K, K, CHK_ABSMAX)) return;
   if constexpr (BF16) {
     const __nv_bfloat16* p = static_cast<const __nv_bfloat16*>(coeffs) + (size_t)s * elems;
     for (size_t e = threadIdx.x; e < elems; e += blockDim.x) m = fmaxf(m, fabsf(__bfloat162float(p[e])));

@@ -33,12 +33,13 @@ cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int
 cudaError_t launch_rows_shrink_t(int M, float2* z, const float* thresh, int N, int nsub,
                                  const float2* tw, cudaStream_t st);
 cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, cudaStream_t st);
+// nimg: image planes of X / acc (bounds of the checked build).
 cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
                              float scale, int Mh, int K, int s0, int S, const float2* tw,
-                             cudaStream_t st);
+                             cudaStream_t st, int nimg);
 cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
-                             const float2* tw, cudaStream_t st);
+                             const float2* tw, cudaStream_t st, int nimg);
 // Pipelined decomposition (both passes in one cooperative launch over a
 // ring of NS staging chunks of CS subbands, col_frac of the CTAs on the
 // column pass); sizes with dec_pipe_supported.
@@ -49,6 +50,8 @@ cudaError_t launch_dec_pipe(int N, int M, bool bf16, const float2* X, float2* ri
                             int CS, int NS, float col_frac, unsigned* ctl, const float2* tw,
                             cudaStream_t st);
 cudaError_t read_pipe_error(unsigned* flag);
+// Guard word of the checked build (fast.cu), read and cleared; 0 otherwise.
+cudaError_t read_check_word(unsigned* word);
 
 // Paired-subband kernels of fused.cu (square planes, see pair_supported):
 // one persistent cluster launch per direction, the plane between the passes

@@ -39,18 +39,21 @@ class ShearletError(RuntimeError):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: libshearlet.so, or with
+    SHL_LIBRARY=checked the bounds-checked build libshearlet_checked.so."""
+    return _build.LIB_CHECKED if os.environ.get("SHL_LIBRARY") == "checked" else _build.LIB
 
 
 def lib():
-    """Load libshearlet.so (built in-tree by ``_build.build()``)."""
+    """Load the library (built in-tree by ``_build.build()``)."""
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(_build.LIB):
-        raise RuntimeError("libshearlet.so is not built: run __graft_entry__.build() "
-                           "or python -m paper_2006_04591_gb300._build")
-    L = ctypes.CDLL(_build.LIB)
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError("%s is not built: run __graft_entry__.build() "
+                           "or python -m paper_2006_04591_gb300._build" % os.path.basename(path))
+    L = ctypes.CDLL(path)
     vp, i, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
     P = ctypes.POINTER
     sig = {
@@ -81,6 +84,8 @@ def lib():
         "shl_subband_absmax": (i, [vp, vp, i, i, i, vp, vp]),
         "shl_iht_thresholds": (i, [vp, vp, i, i, ctypes.c_double, vp, vp]),
         "shl_sync": (i, [vp]),
+        "shl_checked_build": (i, []),
+        "shl_check_status": (i, [i, P(ctypes.c_uint)]),
         "shl_launch_count": (ctypes.c_longlong, []),
         "shl_profile_enable": (i, [i]),
         "shl_profile_read": (i, [ctypes.c_char_p, sz]),
@@ -322,6 +327,17 @@ def shl_adjoint(h, coeffs, dtype, batch, thresh, x_out, ws, stream=None):
 def shl_subband_absmax(h, coeffs, dtype, batch, by_rms, out, stream=None):
     _check("shl_subband_absmax", lib().shl_subband_absmax(
         h, _ptr(coeffs), dtype, batch, int(by_rms), _ptr(out), _stream(stream, out.device)))
+
+
+def shl_checked_build() -> int:
+    return int(lib().shl_checked_build())
+
+
+def shl_check_status(device=0) -> int:
+    """Synchronise `device` and read (and clear) the checked build's guard word."""
+    w = ctypes.c_uint(0)
+    _check("shl_check_status", lib().shl_check_status(int(device), ctypes.byref(w)))
+    return int(w.value)
 
 
 def shl_sync(stream=None):

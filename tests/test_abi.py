@@ -25,6 +25,20 @@ def test_exports_every_header_symbol(L):
     assert missing == []
 
 
+def test_checked_library_exports_the_same_symbols(L):
+    """libshearlet_checked.so (the -DSHL_CHECKED build) carries the same C ABI
+    and says that it is the checked build; the main library says it is not."""
+    import ctypes
+    from paper_2006_04591_gb300 import _build
+    from paper_2006_04591_gb300 import shearlet as S
+    raw = ctypes.CDLL(_build.LIB_CHECKED)
+    for n in S.header_symbols():
+        assert hasattr(raw, n), n
+    raw.shl_checked_build.restype = ctypes.c_int
+    assert raw.shl_checked_build() == 1
+    assert S.shl_checked_build() == 0
+
+
 def test_version_and_status_strings(L):
     assert L.shl_abi_version() == 1
     assert L.shl_status_str(0) == b"ok"
