@@ -350,9 +350,10 @@ shl_status shl_profile_enable(int on);
 shl_status shl_profile_read(char* buf, size_t len);
 
 /* Wait for all work on ``stream``; returns SHL_ECUDA with the CUDA error text
- * if a kernel faulted, and SHL_ETIMEOUT if a bounded wait inside the
- * pipelined decomposition (between its column and row passes, Sec. 3.4)
- * ran out since the last shl_sync on this device; the coefficients of that
+ * if a kernel faulted, and SHL_ETIMEOUT if a bounded device wait ran out
+ * since the last shl_sync on this device: inside the pipelined
+ * decomposition (between its column and row passes, Sec. 3.4), or a row
+ * pass waiting for the bulk copy of an input tile; the results of that
  * call are then incomplete.  The flag is per device (the stream's device),
  * is cleared only here, and while it is set every later pipelined
  * decomposition on that device stops at once and leaves its coefficients

@@ -1147,9 +1147,12 @@ shl_status shl_sync(void* stream) {
   DevGuard g(dev);
   unsigned flag = 0;
   if ((e = shl::read_pipe_error(&flag))) return cuda_fail(e, "shl_sync");
-  if (flag)
+  if (flag & 1u)
     return fail(SHL_ETIMEOUT, "pipelined decomposition: a wait between its passes ran out; the "
                              "coefficients of that call are incomplete");
+  if (flag)
+    return fail(SHL_ETIMEOUT, "a row pass gave up waiting for a bulk copy of its input tile; the "
+                             "results of that call are incomplete");
   return SHL_OK;
 }
 

@@ -55,6 +55,49 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
+// Bounded device waits (the pipelined decomposition's flags, the row tiles'
+// bulk copies) record here why they gave up: bit 0 a pipelined-pass wait,
+// bit 1 a row-tile copy; shl_sync reads and clears it.
+__device__ unsigned int g_pipe_err = 0;
+constexpr unsigned WAIT_PIPE = 1u, WAIT_TILE = 2u;
+constexpr unsigned TILE_SPIN_LIMIT = 1u << 22;   // try_wait rounds, each suspends briefly
+
+// Row tiles of the R2C passes are contiguous runs of global memory (TR whole
+// rows), so one thread moves each with a single bulk copy (TMA,
+// cp.async.bulk) that completes on an mbarrier with its byte count, in
+// place of per-thread 16-byte cp.async: source and destination 16-byte
+// aligned, size a multiple of 16.
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* b) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_addr(b)) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_tx(unsigned long long* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+      ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(b)) : "memory");
+}
+// true once phase `parity` of the barrier has completed; false after
+// TILE_SPIN_LIMIT rounds (the caller records the error and stops).
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* b, unsigned parity) {
+  const unsigned a = smem_addr(b);
+  for (unsigned i = 0; i < TILE_SPIN_LIMIT; ++i) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(a), "r"(parity) : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // Copy `bytes` (multiple of 16) from gmem to smem with all threads of the CTA.
 __device__ __forceinline__ void cta_copy_async(void* dst, const void* src, int bytes, int tid,
                                                int nthreads) {
@@ -138,22 +181,31 @@ __host__ __device__ constexpr int r2c_nst() {
   return 2 * SB + REST <= P::SMEM_CAP ? 2 : (SB + REST <= P::SMEM_CAP ? 1 : 0);
 }
 
+// Thread 0: start the bulk copies of tile t into `stage`, completing on
+// `bar` (one arrival carrying their byte count).  The stage's earlier
+// readers have passed a CTA barrier.
 template <int LOG_M, int INM>
-__device__ __forceinline__ void r2c_issue(const RowsTArgs& a, char* stage, int t, int tid) {
+__device__ __forceinline__ void r2c_issue(const RowsTArgs& a, char* stage, int t,
+                                          unsigned long long* bar) {
   using P = RowsT<LOG_M>;
   const int tiles_per_sub = a.N / P::TR;
   const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
   const size_t row0 = (size_t)s * a.N + y0;
   constexpr int n = P::TR * P::M;
-  if (!SHL_IN(row0 + P::TR - 1, (size_t)a.nsub * a.N, CHK_R2C_IN)) return;
+  if (!SHL_IN(row0 + P::TR - 1, (size_t)a.nsub * a.N, CHK_R2C_IN)) {
+    mbar_arrive_tx(bar, 0);                  // completes the phase without data
+    return;
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   if constexpr (INM == IN_MASKED) {
-    cta_copy_async(stage, static_cast<const float*>(a.in) + row0 * P::M, n * 4, tid, P::THREADS);
-    cta_copy_async(stage + n * 4, a.fest + row0 * P::M, n * 4, tid, P::THREADS);
-    cta_copy_async(stage + n * 8, a.mask + row0 * P::M, n, tid, P::THREADS);
+    mbar_arrive_tx(bar, n * 9);
+    bulk_load(stage, static_cast<const float*>(a.in) + row0 * P::M, n * 4, bar);
+    bulk_load(stage + n * 4, a.fest + row0 * P::M, n * 4, bar);
+    bulk_load(stage + n * 8, a.mask + row0 * P::M, n, bar);
   } else {
     constexpr int esz = RowInput<INM>::ESZ;
-    cta_copy_async(stage, static_cast<const char*>(a.in) + row0 * P::M * esz, n * esz, tid,
-                   P::THREADS);
+    mbar_arrive_tx(bar, n * esz);
+    bulk_load(stage, static_cast<const char*>(a.in) + row0 * P::M * esz, n * esz, bar);
   }
 }
 
@@ -222,20 +274,41 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
   const int tiles_per_sub = a.N / TR;
   const int ntiles = a.nsub * tiles_per_sub;
 
+  __shared__ unsigned long long full[2];   // one mbarrier per stage
+  if (tid == 0) {
+    mbar_init(&full[0]);
+    mbar_init(&full[1]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
   LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
-  if (NST == 2 && blockIdx.x < ntiles) r2c_issue<LOG_M, INM>(a, stages, blockIdx.x, tid);
-  cp_async_commit();
+  __syncthreads();
+  if (NST == 2 && tid == 0 && blockIdx.x < ntiles)
+    r2c_issue<LOG_M, INM>(a, stages, blockIdx.x, &full[0]);
   int k = 0;
+  int pending = NST == 2 && blockIdx.x < ntiles ? 1 : 0;    // copies issued, not yet waited on
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     if constexpr (NST > 0) {
       const int tn = NST == 2 ? t + gridDim.x : t;
-      if (tn < ntiles) r2c_issue<LOG_M, INM>(a, stages + ((k + 1) % NST) * SB, tn, tid);
-      cp_async_commit();
-      if (NST == 2) cp_async_wait1(); else cp_async_wait0();
+      if (tn < ntiles) {
+        if (tid == 0) r2c_issue<LOG_M, INM>(a, stages + ((k + 1) % NST) * SB, tn, &full[(k + 1) % NST]);
+        ++pending;
+      }
+      // tile k's copy: stage k % NST, its (k / NST)-th use
+      const bool ok = mbar_wait_bounded(&full[k % NST], (k / NST) & 1);
+      --pending;
+      if (__syncthreads_or(!ok)) {             // the same decision in every thread
+        if (tid == 0) {
+          atomicOr(&g_pipe_err, WAIT_TILE);
+          // a copy still in flight targets the other stage: let it land
+          if (pending > 0) mbar_wait_bounded(&full[(k + 1) % NST], ((k + 1) / NST) & 1);
+        }
+        return;
+      }
+    } else {
+      __syncthreads();
     }
-    __syncthreads();
     const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
     // tile input: staged in shared memory, or the global rows themselves
     const char* cur = NST > 0 ? stages + (k % (NST > 0 ? NST : 1)) * SB : nullptr;
@@ -281,7 +354,6 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
     r2c_tile_finish<LOG_M>(v, line, tile, twl, ptw, a.out + (size_t)s * Mh * a.N + y0, a.N, r, j,
                            valid, tid, tile_ok);    // ends with a barrier: tile and stage reusable
   }
-  cp_async_wait0();
 }
 
 struct RowsTC2RArgs {
@@ -703,8 +775,6 @@ __global__ void __launch_bounds__(256, LinesT<LOG_N>::R >= 32 ? 1 : 2) k_rec_lin
 // claimed in chunk order, and the cooperative launch keeps every CTA
 // resident, so every wait ends.  Each wait is also bounded: when it runs
 // out the CTA sets g_pipe_err, and every CTA leaves at its next claim.
-__device__ unsigned int g_pipe_err = 0;
-
 constexpr unsigned PIPE_SPIN_LIMIT = 1u << 21;   // ~0.3-1 s with the back-off below
 
 struct DecPipeArgs {
