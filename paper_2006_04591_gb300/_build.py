@@ -23,7 +23,8 @@ CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
-CU_SOURCES = ["fast.cu", "fused.cu", "general.cu", "noalloc.cu", "nn.cu", "nn_tc.cu", "bank_gpu.cu", "ray.cu"]
+CU_SOURCES = ["fast.cu", "fused.cu", "general.cu", "noalloc.cu", "nn.cu", "nn_tc.cu", "bank_gpu.cu", "ray.cu",
+              "tc_dft.cu"]
 CPP_SOURCES = ["api.cpp", "bank_build.cpp"]
 # The checked library: every source again with -DSHL_CHECKED (bounds guards
 # with a device error word in the transform kernels), the same C ABI.

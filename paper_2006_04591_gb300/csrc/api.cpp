@@ -178,6 +178,18 @@ bool fused_on() {
   }();
   return on;
 }
+// Tensor-core column pass of the bfloat16-output decomposition
+// (tc_dft.cu): SHL_TC_DFT=1 turns it on, read once per process.
+bool tc_dft_on() {
+  static const bool on = [] {
+    const char* e = std::getenv("SHL_TC_DFT");
+    return e && e[0] == '1';
+  }();
+  return on;
+}
+bool use_tc_dft(const shl_bank* b, shl_dtype dtype) {
+  return dtype == SHL_BF16 && !b->general && tc_dft_on() && shl::dec_lines_tc_supported(b->N, b->Mh);
+}
 // Co-resident clusters of the paired kernels on the bank's device (0 when
 // the query fails, which keeps the staged kernels).
 int pair_ncl_max(const shl_bank* b) {
@@ -451,9 +463,13 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
     return SHL_OK;
   }
   const int S = stage_override > 0 ? stage_override : stage_subbands(b);
+  const bool tc = use_tc_dft(b, dtype);
   for (int s0 = 0; s0 < total; s0 += S) {
     const int Sc = std::min(S, total - s0);
-    {
+    if (tc) {
+      Launch L_("dec_lines_tc", st);
+      e = shl::launch_dec_lines_tc(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
+    } else {
       Launch L_("dec_lines", st);
       e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
     }
@@ -1125,6 +1141,9 @@ shl_status shl_check_status(int device, unsigned* word) {
   DevGuard g(device);
   cudaError_t e = cudaDeviceSynchronize();
   if (!e) e = shl::read_check_word(word);
+  unsigned w2 = 0;
+  if (!e) e = shl::read_check_word_tc(&w2);
+  if (!e) *word |= w2;
   if (e) return cuda_fail(e, "shl_check_status");
   return SHL_OK;
 }
@@ -1145,8 +1164,12 @@ shl_status shl_sync(void* stream) {
   int dev = -1;
   if ((e = cudaStreamGetDevice(st, &dev))) return cuda_fail(e, "shl_sync");
   DevGuard g(dev);
-  unsigned flag = 0;
+  unsigned flag = 0, dft = 0;
   if ((e = shl::read_pipe_error(&flag))) return cuda_fail(e, "shl_sync");
+  if ((e = shl::read_dft_error(&dft))) return cuda_fail(e, "shl_sync");
+  if (dft)
+    return fail(SHL_ETIMEOUT, "tensor-core column pass: a wait for its MMAs ran out; the "
+                             "coefficients of that call are incomplete");
   if (flag & 1u)
     return fail(SHL_ETIMEOUT, "pipelined decomposition: a wait between its passes ran out; the "
                              "coefficients of that call are incomplete");

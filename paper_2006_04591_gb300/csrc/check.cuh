@@ -21,11 +21,13 @@
 #endif
 
 namespace shl {
-// Guard bits of fast.cu.
+// Guard bits of the transform kernels.
 enum CheckCode : unsigned {
   CHK_R2C_IN = 1u << 0, CHK_R2C_OUT = 1u << 1, CHK_C2R_IN = 1u << 2, CHK_C2R_OUT = 1u << 3,
   CHK_LINES = 1u << 4, CHK_DEC_X = 1u << 5, CHK_DEC_G = 1u << 6, CHK_DEC_OUT = 1u << 7,
   CHK_REC_STAGE = 1u << 8, CHK_REC_G = 1u << 9, CHK_REC_ACC = 1u << 10, CHK_SHRINK = 1u << 11,
   CHK_ABSMAX = 1u << 12,
+  // tc_dft.cu
+  CHK_TC_X = 1u << 13, CHK_TC_G = 1u << 14, CHK_TC_OUT = 1u << 15,
 };
 }  // namespace shl

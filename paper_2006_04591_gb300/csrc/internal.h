@@ -40,6 +40,16 @@ cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G
 cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
                              const float2* tw, cudaStream_t st, int nimg);
+// Column pass of the bfloat16-output decomposition on the tensor cores
+// (tc_dft.cu, N = 512 only): the same staging planes as launch_dec_lines.
+bool dec_lines_tc_supported(int N, int Mh);
+cudaError_t launch_dec_lines_tc(int N, const float2* X, float2* out, const float* G,
+                                const float* invW, float scale, int Mh, int K, int s0, int S,
+                                const float2* tw, cudaStream_t st, int nimg);
+// Error flag of its bounded MMA waits and its checked-build guard word,
+// read and cleared.
+cudaError_t read_dft_error(unsigned* flag);
+cudaError_t read_check_word_tc(unsigned* word);
 // Pipelined decomposition (both passes in one cooperative launch over a
 // ring of NS staging chunks of CS subbands, col_frac of the CTAs on the
 // column pass); sizes with dec_pipe_supported.

@@ -4,7 +4,7 @@
     python -m paper_2006_04591_gb300.measure --case N B
     python -m paper_2006_04591_gb300.measure --general [--out FILE]
 
-``--case N B`` runs only two decomposition + reconstruction passes of B
+``--case N B [--bf16]`` runs only two decomposition + reconstruction passes of B
 cartoon images of N x N with the 4-scale bank (49 filters): the small case
 that the ncu captures under profiles/ are taken on (launch order per pass:
 image R2C rows, image spectrum lines, coefficient lines, coefficient C2R
@@ -137,16 +137,17 @@ def ray_point(N, A, B):
             "adjoint_samples_per_s": samples / ta}
 
 
-def small_case(N, B):
+def small_case(N, B, bf16=False):
     bank = Bank.create(N, N, 4, device=0)
     x = torch.from_numpy(np.stack([synth.cartoon(N, N, s) for s in range(B)]).astype(np.float32)).cuda()
+    dt = torch.bfloat16 if bf16 else torch.float32
     for _ in range(2):
-        c = bank.decompose(x)
+        c = bank.decompose(x, dtype=dt)
         r = bank.reconstruct(c)
     torch.cuda.synchronize()
     err = (r - x).abs().max().item()
-    print("case %dx%d B=%d K=%d: max |rec - x| = %.3g" % (N, N, B, bank.K, err))
-    if not err <= 1e-5 * x.abs().max().item():
+    print("case %dx%d B=%d K=%d %s: max |rec - x| = %.3g" % (N, N, B, bank.K, dt, err))
+    if not err <= (1e-2 if bf16 else 1e-5) * x.abs().max().item():
         raise SystemExit("perfect reconstruction failed")
 
 
@@ -174,13 +175,14 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--out", default=None)
     ap.add_argument("--case", type=int, nargs=2, metavar=("N", "B"), default=None)
+    ap.add_argument("--bf16", action="store_true", help="--case with bfloat16 coefficients")
     ap.add_argument("--general", action="store_true")
     ap.add_argument("--ray", action="store_true")
     args = ap.parse_args()
     from . import _build
     _build.build()
     if args.case:
-        small_case(*args.case)
+        small_case(*args.case, bf16=args.bf16)
         return
     if args.ray:
         pts = [ray_point(128, 30, 32), ray_point(512, 180, 8), ray_point(1024, 360, 1)]
