@@ -100,7 +100,7 @@ def kernel_alg_bytes(name, B, K, N, M, s=4):
     img, coef, filt = B * N * M * 4, B * K * N * M * s, K * H * 4
     return {
         "rows_r2c_image": img, "rows_c2r_image": img, "lines_fwd_image": 0,
-        "dec_lines": filt, "rec_lines": filt + H * 4,
+        "dec_lines": filt, "dec_lines_tc": filt, "rec_lines": filt + H * 4,
         "rows_c2r_coeffs": coef, "rows_r2c_coeffs": coef,
         "pair_dec": coef + filt, "pair_rec": coef + filt, "pair_final": H * 4,
         "dec_pipe": coef + filt, "rows_shrink": 0,
