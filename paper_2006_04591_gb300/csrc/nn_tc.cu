@@ -122,13 +122,15 @@ __device__ __forceinline__ void tc_fence_after() {
 
 template <int CG, int NP>
 struct ConvTcT {
-  static_assert(CG % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 64, "tile shape");
+  static_assert(CG % 2 == 0 && NP % 16 == 0 && NP >= 16 && NP <= 128, "tile shape");
   static constexpr int KS = CG / 2;                          // K steps of 16 per tap
   static constexpr int SLOTS = 4;                            // input-row ring
   static constexpr size_t WBYTES = (size_t)9 * CG * NP * 16;  // [tap][cg][n][8]
   static constexpr size_t RBYTES = (size_t)CG * PW * 16;      // one row: [cg][px][8]
   static constexpr size_t SMEM = WBYTES + SLOTS * RBYTES;    // descriptors stay inside
-  static constexpr uint32_t NCOLS = NP <= 32 ? 32 : 64;       // TMEM columns (power of 2)
+  static constexpr uint32_t NCOLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : 128);   // TMEM columns (power of 2)
+  // two CTAs per SM where their shared memory fits (228 KB, 1 KB reserved each)
+  static constexpr int MINB = 2 * (SMEM + 1024) <= 228 * 1024 ? 2 : 1;
 };
 
 // Staging of one input row in two halves (global loads into registers, then
@@ -194,7 +196,7 @@ __device__ __forceinline__ void conv_store_row(const ConvRegs<CG>& R, uint8_t* d
 // y + 2 is staged while the MMAs of row y run, so each output row costs one
 // new input row.
 template <int CG, int NP>
-__global__ void __launch_bounds__(CONV_THREADS, 2) k_conv3x3_tc(ConvTcArgs a) {
+__global__ void __launch_bounds__(CONV_THREADS, (ConvTcT<CG, NP>::MINB)) k_conv3x3_tc(ConvTcArgs a) {
   using P = ConvTcT<CG, NP>;
   extern __shared__ __align__(128) uint8_t sm[];
   uint8_t* wsm = sm;
@@ -349,7 +351,8 @@ struct WgradTcT {
   static constexpr size_t ABYTES = (size_t)PG * 128 * 16;   // one input row: [pg][r][8]
   static constexpr size_t BBYTES = (size_t)PG * NP * 16;    // one gout row: [pg][o][8]
   static constexpr size_t SMEM = SLOTS * ABYTES + 2 * BBYTES;
-  static constexpr uint32_t NCOLS = 3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : 256);
+  static constexpr uint32_t NCOLS =
+      3 * NP <= 64 ? 64 : (3 * NP <= 128 ? 128 : (3 * NP <= 256 ? 256 : 512));
   static constexpr int BITEMS = (NP * PG + THREADS - 1) / THREADS;   // gout items per thread
   static constexpr int IITEMS = (42 * PG + THREADS - 1) / THREADS;   // input items (Cin <= 42)
 };
@@ -586,18 +589,20 @@ __global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcAr
     float* part = a.part + (size_t)blockIdx.x * stride;
 #pragma unroll
     for (int dy = 0; dy < 3; ++dy) {
-      uint32_t acc[NP];
+#pragma unroll 1
+      for (int q = 0; q < NP / 16; ++q) {          // 16 columns (output channels) at a time
+        uint32_t acc[16];
+        SHL_TMEM_LD16(acc, tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dy * NP + 16 * q));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (dx < 3) {
 #pragma unroll
-      for (int q = 0; q < NP / 16; ++q)
-        SHL_TMEM_LD16(acc + 16 * q,
-                      tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(dy * NP + 16 * q));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (dx < 3) {
-#pragma unroll
-        for (int o = 0; o < NP; ++o)
-          if (o < a.Cout)
-            part[(((size_t)o * a.Cin + i) * 3 + dy) * 3 + dx] =
-                blockIdx.x < nunits ? __uint_as_float(acc[o]) : 0.f;
+          for (int j = 0; j < 16; ++j) {
+            const int o = 16 * q + j;
+            if (o < a.Cout)
+              part[(((size_t)o * a.Cin + i) * 3 + dy) * 3 + dx] =
+                  blockIdx.x < nunits ? __uint_as_float(acc[j]) : 0.f;
+          }
+        }
       }
     }
   }
@@ -972,14 +977,42 @@ bool conv_ws_enabled() {
 
 int round16(int v) { return (v + 15) / 16 * 16; }
 
+// Tile of one call: CG 8-channel input groups, NP output channels (padded to
+// 16).  Narrow layers take the exact tile (and the warp-specialised variant
+// when it is switched on); layers with up to 112 input and 32 output
+// channels, or 32 input and 112 output channels, take a wider tile with the
+// extra channels zero.  false: no tile takes the shape.
+bool tc_tile(int Ci, int Co, int* cg, int* np) {
+  if (Ci < 1 || Co < 1) return false;
+  *cg = round16(Ci) / 8;
+  *np = round16(Co);
+  if (*cg <= 6 && *np <= 48) return true;
+  if (*cg <= 14 && *np <= 32) {
+    *np = 32;
+    return true;
+  }
+  if (*cg <= 4 && *np <= 112) {
+    *cg = 4;
+    *np = *np <= 64 ? 64 : (*np <= 96 ? 96 : 112);
+    return true;
+  }
+  return false;
+}
+
 cudaError_t dispatch(const ConvTcArgs& a, cudaStream_t st) {
-  const int cg = round16(a.Cin) / 8, np = round16(a.Cout);
+  int cg = 0, np = 0;
+  if (!tc_tile(a.Cin, a.Cout, &cg, &np)) return cudaErrorInvalidValue;
 #define SHL_TC(CGV, NPV)                                                                \
   if (cg == CGV && np == NPV)                                                            \
     return conv_ws_enabled() ? launch_ws<CGV, NPV>(a, st) : launch_tc<CGV, NPV>(a, st);
+#define SHL_TC_WIDE(CGV, NPV) \
+  if (cg == CGV && np == NPV) return launch_tc<CGV, NPV>(a, st);
   SHL_TC(2, 16) SHL_TC(2, 32) SHL_TC(2, 48)
   SHL_TC(4, 16) SHL_TC(4, 32) SHL_TC(4, 48)
   SHL_TC(6, 16) SHL_TC(6, 32) SHL_TC(6, 48)
+  SHL_TC_WIDE(8, 32) SHL_TC_WIDE(10, 32) SHL_TC_WIDE(12, 32) SHL_TC_WIDE(14, 32)
+  SHL_TC_WIDE(4, 64) SHL_TC_WIDE(4, 96) SHL_TC_WIDE(4, 112)
+#undef SHL_TC_WIDE
 #undef SHL_TC
   return cudaErrorInvalidValue;
 }
@@ -1001,7 +1034,8 @@ shl_status tc_run(const ConvTcArgs& a, void* stream, const char* where) {
 extern "C" {
 
 int shl_nn_conv3x3_tc_supported(int Ci, int Co, int H, int W) {
-  return Ci >= 1 && Ci <= 48 && Co >= 1 && Co <= 48 && H >= 1 && W >= TC_M && W % TC_M == 0;
+  int cg = 0, np = 0;
+  return tc_tile(Ci, Co, &cg, &np) && H >= 1 && W >= TC_M && W % TC_M == 0;
 }
 
 shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const float* bias,
@@ -1029,7 +1063,7 @@ shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, fl
 }
 
 int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W) {
-  return Ci >= 1 && 3 * Ci <= 128 && Co >= 1 && Co <= 48 && H >= 1 && W >= TC_M && W % TC_M == 0;
+  return Ci >= 1 && 3 * Ci <= 128 && Co >= 1 && Co <= 96 && H >= 1 && W >= TC_M && W % TC_M == 0;
 }
 
 size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W) {
@@ -1051,10 +1085,11 @@ shl_status shl_nn_conv3x3_backward_weight_tc(const float* in, const float* gout,
   int grid = 0, ru = 0;
   wgrad_plan(B, H, W, &grid, &ru);
   const WgradTcArgs a{in, gout, ws, B, Ci, Co, H, W, ru};
-  const int np = round16(Co);
+  const int np = round16(Co);          // 49..96 output channels: the 96-wide tile
   cudaError_t e = np == 16 ? launch_wgrad<16>(a, grid, st)
                 : np == 32 ? launch_wgrad<32>(a, grid, st)
-                           : launch_wgrad<48>(a, grid, st);
+                : np == 48 ? launch_wgrad<48>(a, grid, st)
+                           : launch_wgrad<96>(a, grid, st);
   if (e == cudaSuccess) {
     const int nw = Co * Ci * 9;
     k_wgrad_reduce<<<(nw + Co + 255) / 256, 256, 0, st>>>(ws, gw, gb, grid, nw, Co);

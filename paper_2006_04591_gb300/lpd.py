@@ -183,15 +183,53 @@ def cosine_lr(lr, it, sched_steps):
     return 0.5 * lr * (1.0 + math.cos(math.pi * min(it, sched_steps) / sched_steps))
 
 
+class _GraphStep:
+    """Forward and backward of one training step captured in a CUDA graph.
+
+    The step issues about a thousand kernel launches from Python (ten
+    unrolled iterations of two three-layer networks, the ray transform and
+    the shearlet transforms, forward and backward), so replaying them as one
+    graph removes the per-launch host cost.  The batch is copied into static
+    input buffers before each replay; the gradients the graph writes stay in
+    the tensors autograd allocated during capture, which are handed back to
+    the parameters before the (eager) clipping and Adam update, since
+    clipping may rebind ``p.grad``.  Every kernel of the step is
+    deterministic, so a replay computes what the eager step would.  No
+    autograd graph of an earlier step may be alive at capture: its gradient
+    accumulators keep the stream they were made on."""
+
+    def __init__(self, net, params, g, f_true):
+        self.params = params
+        self.g = g.clone()
+        self.f = f_true.clone()
+        for p in params:
+            p.grad = None
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self.loss = NN.mse(net(self.g), self.f)
+            self.loss.backward()
+        self.grads = [p.grad for p in params]
+
+    def run(self, g, f_true):
+        self.g.copy_(g)
+        self.f.copy_(f_true)
+        self.graph.replay()
+        for p, gr in zip(self.params, self.grads):
+            p.grad = gr
+        return self.loss
+
+
 def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=0, scales=2,
-          log_every=100, checkpoint=None, ckpt_every=500):
+          log_every=100, checkpoint=None, ckpt_every=500, graph=True):
     """Train the ``domain`` network for ``steps`` steps.  With ``checkpoint``
     (a file path) the state is written there every ``ckpt_every`` steps and
     at the end (atomically), and an existing checkpoint is resumed:
     parameters, Adam state and step, with its learning-rate schedule (total
     steps and rate) kept, while the data stream restarts at that step's
     seeds.  A checkpoint of another domain, size, angle count or scale count
-    is refused (ValueError)."""
+    is refused (ValueError).  ``graph``: after the first (eager) step,
+    forward and backward replay as one CUDA graph (_GraphStep); the
+    gradient clipping and the Adam update stay eager."""
     op = RayTransform(N, A, device=0)
     bank = Bank.create(N, N, scales, device=0) if domain == "shearlet" else None
     net = LPD(op, domain, bank, seed=seed)
@@ -210,16 +248,26 @@ def train(domain, steps=1000, batch=4, N=128, A=30, n_train=2000, lr=1e-3, seed=
         gen = torch.Generator(device="cuda").manual_seed(seed + 7 + 1000003 * start)
     meta = {"domain": domain, "size": N, "angles": A, "scales": scales, "batch": batch,
             "n_train": n_train, "seed": seed, "steps": sched_steps, "lr": base_lr}
+    gstep = None
     for it in range(start, steps):
         opt.lr = cosine_lr(base_lr, it, sched_steps)
         idx = torch.from_numpy(rng.integers(0, n_train, batch)).cuda()
         f_true = pool[idx].contiguous()
         g = noisy_data(op, f_true, gen)
+        if graph and gstep is None and it > start:
+            # captured after one eager step; the eager step's autograd graph
+            # is dropped first, so that the parameters' gradient accumulators
+            # are made anew (on the capture stream) inside the capture
+            loss = None
+            gstep = _GraphStep(net, params, g, f_true)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        opt.zero_grad()
-        loss = NN.mse(net(g), f_true)
-        loss.backward()
+        if gstep is not None:
+            loss = gstep.run(g, f_true)
+        else:
+            opt.zero_grad()
+            loss = NN.mse(net(g), f_true)
+            loss.backward()
         NN.clip_grad_norm(params, 1.0)
         opt.step()
         torch.cuda.synchronize()

@@ -148,8 +148,18 @@ def shl_nn_conv3x3_backward(x, w, gout, need_gin=True, tc=False, tc_w=False):
     L = lib()
     gw = torch.empty_like(w)
     gb = torch.empty(Co, dtype=torch.float32, device=x.device)
-    if tc_w:
+    if tc_w and Ci <= TC_WCH:
         shl_nn_conv3x3_backward_weight_tc(x, gout, gw, gb)
+    elif tc_w:
+        # one call stages at most 42 input channels (3 Ci <= 128 rows); the
+        # weight gradient of an input-channel group depends on that group only
+        for k, (c0, c1) in enumerate(_groups(Ci, TC_WCH)):
+            gwg = torch.empty((Co, c1 - c0, 3, 3), dtype=torch.float32, device=x.device)
+            gbg = torch.empty(Co, dtype=torch.float32, device=x.device)
+            shl_nn_conv3x3_backward_weight_tc(x[:, c0:c1].contiguous(), gout, gwg, gbg)
+            gw[:, c0:c1] = gwg
+            if k == 0:
+                gb.copy_(gbg)
     ws = _ws(L.shl_nn_conv3x3_workspace_floats(B, Ci, Co, H, W), x) if (not tc_w or
                                                                       (need_gin and not tc)) else None
     if not tc_w and Ci <= 64:
@@ -271,7 +281,7 @@ class _Conv3x3(torch.autograd.Function):
         # tensor cores for each pass where one call takes the shape
         ctx.tc_fwd = bool(tc) and shl_nn_conv3x3_tc_supported(Ci, Co, H, W)
         ctx.tc_bwd = bool(tc) and shl_nn_conv3x3_tc_supported(Co, Ci, H, W)
-        ctx.tc_w = bool(tc) and shl_nn_conv3x3_wgrad_tc_supported(Ci, Co, H, W)
+        ctx.tc_w = bool(tc) and shl_nn_conv3x3_wgrad_tc_supported(min(Ci, TC_WCH), Co, H, W)
         if ctx.tc_fwd:
             shl_nn_conv3x3_forward_tc(x, w.contiguous(), b.contiguous(), out)
         else:

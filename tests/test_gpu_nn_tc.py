@@ -25,8 +25,12 @@ def _bf(t):
     return t.to(torch.bfloat16).double()
 
 
+# the last six take the wide tiles: up to 112 input channels with at most 32
+# outputs, or at most 32 inputs with up to 112 outputs (padded channels zero)
 SHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 16, 16, 3, 384),
-          (1, 48, 48, 2, 128), (3, 32, 32, 1, 128), (1, 7, 5, 6, 256)]
+          (1, 48, 48, 2, 128), (3, 32, 32, 1, 128), (1, 7, 5, 6, 256),
+          (1, 102, 32, 3, 128), (2, 32, 85, 2, 128), (1, 85, 32, 2, 128), (1, 32, 102, 2, 128),
+          (1, 64, 16, 2, 128), (1, 16, 60, 2, 256)]
 
 
 @pytest.mark.parametrize("B,Ci,Co,H,W", SHAPES)
@@ -60,7 +64,8 @@ def test_tc_backward_data_matches_rounded_oracle(B, Ci, Co, H, W):
 
 
 WSHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 42, 48, 2, 128),
-           (3, 32, 16, 1, 128), (1, 7, 5, 6, 256)]
+           (3, 32, 16, 1, 128), (1, 7, 5, 6, 256), (1, 32, 85, 3, 128), (2, 16, 96, 2, 128),
+           (1, 42, 60, 2, 256)]
 
 
 @pytest.mark.parametrize("B,Ci,Co,H,W", WSHAPES)
@@ -83,8 +88,12 @@ def test_tc_rejects_unsupported_shapes():
     from paper_2006_04591_gb300 import nn
     from paper_2006_04591_gb300.shearlet import ShearletError
     assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 100)
-    assert not nn.shl_nn_conv3x3_tc_supported(64, 32, 8, 128)
+    assert not nn.shl_nn_conv3x3_tc_supported(120, 32, 8, 128)     # more than 112 inputs
+    assert not nn.shl_nn_conv3x3_tc_supported(64, 64, 8, 128)      # wide on both sides
+    assert not nn.shl_nn_conv3x3_tc_supported(48, 80, 8, 128)
+    assert not nn.shl_nn_conv3x3_tc_supported(32, 120, 8, 128)
     assert not nn.shl_nn_conv3x3_wgrad_tc_supported(43, 32, 8, 128)
+    assert not nn.shl_nn_conv3x3_wgrad_tc_supported(32, 97, 8, 128)
     x = torch.zeros((1, 32, 8, 100), device="cuda")
     with pytest.raises(ShearletError):
         nn.shl_nn_conv3x3_forward_tc(x, torch.zeros((32, 32, 3, 3), device="cuda"), None,
@@ -171,11 +180,15 @@ def test_warp_specialised_conv_matches_rounded_oracle():
     assert "ws ok" in r.stdout
 
 
-@pytest.mark.parametrize("B,Ci,Co,H,W", [(2, 102, 32, 3, 128), (1, 32, 85, 4, 128),
-                                         (1, 102, 85, 2, 256), (2, 7, 32, 3, 256)])
-def test_grouped_tc_conv_autograd_matches_rounded_oracle(B, Ci, Co, H, W):
-    # layers wider than one tensor-core call (the shearlet-domain primal
-    # networks of the learned primal-dual reconstruction): channel groups
+@pytest.mark.parametrize("tc,B,Ci,Co,H,W", [
+    ("grouped", 2, 102, 32, 3, 128), ("grouped", 1, 32, 85, 4, 128),
+    ("grouped", 1, 102, 85, 2, 256), ("grouped", 2, 7, 32, 3, 256),
+    (True, 2, 102, 32, 3, 128), (True, 1, 32, 85, 4, 128), (True, 2, 85, 32, 2, 128)])
+def test_wide_tc_conv_autograd_matches_rounded_oracle(tc, B, Ci, Co, H, W):
+    # the shearlet-domain primal layers of the learned primal-dual
+    # reconstruction (102 -> 32, 32 -> 85): tc=True takes them in one call per
+    # pass on the wide tiles (the weight gradient of 102 inputs in groups of
+    # 42), tc="grouped" in channel groups of at most 48
     from paper_2006_04591_gb300 import nn
     gen = torch.Generator().manual_seed(Ci * 100 + Co)
     x = torch.randn((B, Ci, H, W), generator=gen)
@@ -185,7 +198,7 @@ def test_grouped_tc_conv_autograd_matches_rounded_oracle(B, Ci, Co, H, W):
     xg = x.cuda().requires_grad_(True)
     wg = w.cuda().requires_grad_(True)
     bg = b.cuda().requires_grad_(True)
-    y = nn.conv3x3(xg, wg, bg, tc="grouped")
+    y = nn.conv3x3(xg, wg, bg, tc=tc)
     (y * go.cuda()).sum().backward()
     nn.shl_nn_tc_status()
     assert _rel(y, ON.conv3x3(_bf(x), _bf(w), b.double())) <= TOL
