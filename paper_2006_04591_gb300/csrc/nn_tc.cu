@@ -6,7 +6,8 @@
 // with P_tap[m][ci] = in[ci][y + dy - 1][x0 + m + dx - 1] (zero padding).
 // The CTA stages input rows as bfloat16 in the no-swizzle K-major
 // core-matrix layout [ci/8][pixel][8 ci] (16 bytes per pixel and channel
-// group), loading float4 groups of 4 pixels, into a ring of four rows.  Consecutive pixels are 16 bytes apart, so
+// group), loading groups of 4 pixels (float4, or two float2 when the width is
+// not a multiple of 4), into a ring of four rows.  Consecutive pixels are 16 bytes apart, so
 // the A operand of tap (dy, dx) is the same staged rows with its start
 // address moved by dx * 16 bytes: no im2col copy.  The weights sit in the
 // same layout [tap][ci/8][n][8 ci] for the whole launch.  One thread issues
@@ -31,10 +32,10 @@ __device__ unsigned int g_tc_err = 0;
 
 constexpr int TC_M = 128;            // output pixels per tile (MMA M)
 constexpr int CONV_THREADS = 256;    // warps w and w + 4 share TMEM lanes 32 (w % 4)
-// Staged pixels per row: x0 - 4 .. x0 + 131, in float4 groups aligned to 16
-// bytes (x0 and W are multiples of 128, so each group lies wholly inside or
-// wholly outside the image); output pixel m, tap dx reads staged pixel
-// m + dx + 3.
+// Staged pixels per row: x0 - 4 .. x0 + 131 (x0 a multiple of 128), in groups
+// of 4 (load4: zero outside the row, so the last tile of a row whose width
+// is not a multiple of 128 is ragged); output pixel m, tap dx reads staged
+// pixel m + dx + 3.  Widths are even (float2 halves stay 8-byte aligned).
 constexpr int PW = TC_M + 8;
 constexpr int PX0 = 3;
 constexpr unsigned TC_SPIN_LIMIT = 1u << 22;
@@ -145,6 +146,21 @@ struct ConvRegs {
   float4 v[ITEMS][8];
 };
 
+// Pixels gx .. gx + 3 (gx a multiple of 4) of the row starting at `row`, zero
+// outside 0 .. W - 1: one float4 when W is a multiple of 4 (the group then
+// lies wholly inside or wholly outside the row), else (W even, rows 8-byte
+// aligned) two float2 halves, each wholly inside or outside.
+__device__ __forceinline__ float4 load4(const float* row, int gx, int W) {
+  if ((W & 3) == 0)
+    return gx >= 0 && gx < W ? __ldg(reinterpret_cast<const float4*>(row + gx))
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+  const float2 lo = gx >= 0 && gx < W ? __ldg(reinterpret_cast<const float2*>(row + gx))
+                                      : make_float2(0.f, 0.f);
+  const float2 hi = gx + 2 >= 0 && gx + 2 < W ? __ldg(reinterpret_cast<const float2*>(row + gx + 2))
+                                              : make_float2(0.f, 0.f);
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 template <int CG>
 __device__ __forceinline__ void conv_load_row(const ConvTcArgs& a, ConvRegs<CG>& R, int b, int gy,
                                               int x0, int tid) {
@@ -156,11 +172,11 @@ __device__ __forceinline__ void conv_load_row(const ConvTcArgs& a, ConvRegs<CG>&
     const int idx = tid + k * CONV_THREADS;
     const int cg = idx / PG, q = idx - cg * PG;
     const int gx = x0 - 4 + 4 * q;
-    const bool ok = rok && idx < CG * PG && gx >= 0 && gx < a.W;
-    const float* src = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W + (ok ? gx : 0);
+    const bool ok = rok && idx < CG * PG;
+    const float* row = a.in + (((size_t)b * a.Cin + cg * 8) * a.H + (ok ? gy : 0)) * a.W;
 #pragma unroll
     for (int c = 0; c < 8; ++c)
-      R.v[k][c] = (ok && cg * 8 + c < a.Cin) ? __ldg(reinterpret_cast<const float4*>(src + c * cs))
+      R.v[k][c] = (ok && cg * 8 + c < a.Cin) ? load4(row + c * cs, gx, a.W)
                                              : make_float4(0.f, 0.f, 0.f, 0.f);
   }
 }
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(CONV_THREADS, (ConvTcT<CG, NP>::MINB)) k_conv3
   const uint32_t wbase = smem_u32(wsm), rbase = smem_u32(ring);
   const size_t cs = (size_t)a.H * a.W;
 
-  const int tiles_x = a.W / TC_M;
+  const int tiles_x = (a.W + TC_M - 1) / TC_M;
   const int RU = a.rows_per_unit;
   const int runs = (a.H + RU - 1) / RU;
   const int nunits = a.B * tiles_x * runs;
@@ -307,11 +323,13 @@ __global__ void __launch_bounds__(CONV_THREADS, (ConvTcT<CG, NP>::MINB)) k_conv3
       for (int q = 0; q < HC / 8; ++q)
         SHL_TMEM_LD8(acc + 8 * q, tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(n0 + 8 * q));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + x0 + quarter * 32 + lane;
+      const int px = x0 + quarter * 32 + lane;     // the last tile of a row may be ragged
+      float* o = a.out + (((size_t)b * a.Cout) * a.H + y) * a.W + px;
 #pragma unroll
       for (int n = 0; n < HC; ++n) {
         const int ch = n0 + n;
-        if (ch < a.Cout) o[ch * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + ch) : 0.f);
+        if (ch < a.Cout && px < a.W)
+          o[ch * cs] = __uint_as_float(acc[n]) + (a.bias ? __ldg(a.bias + ch) : 0.f);
       }
       tc_fence_before();   // TMEM reads done before the next row's MMAs (barrier at loop top)
     }
@@ -380,13 +398,21 @@ __device__ __forceinline__ void wgrad_load_in(const WgradTcArgs& a, WgradRegs<NP
     if (rok && idx < a.Cin * P::PG) {
       const int pg = idx / a.Cin, i = idx - pg * a.Cin;
       const int xs = x0 + 8 * pg;
-      const float* src = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W + xs;
-      const float4 v0 = __ldg(reinterpret_cast<const float4*>(src));
-      const float4 v1 = __ldg(reinterpret_cast<const float4*>(src + 4));
-      e[0] = xs > 0 ? __ldg(src - 1) : 0.f;
-      e[1] = v0.x; e[2] = v0.y; e[3] = v0.z; e[4] = v0.w;
-      e[5] = v1.x; e[6] = v1.y; e[7] = v1.z; e[8] = v1.w;
-      e[9] = xs + 8 < a.W ? __ldg(src + 8) : 0.f;
+      const float* row = a.in + (((size_t)b * a.Cin + i) * a.H + gy) * a.W;
+      if ((a.W & 3) == 0 && xs + 8 <= a.W) {
+        const float4 v0 = __ldg(reinterpret_cast<const float4*>(row + xs));
+        const float4 v1 = __ldg(reinterpret_cast<const float4*>(row + xs + 4));
+        e[0] = xs > 0 ? __ldg(row + xs - 1) : 0.f;
+        e[1] = v0.x; e[2] = v0.y; e[3] = v0.z; e[4] = v0.w;
+        e[5] = v1.x; e[6] = v1.y; e[7] = v1.z; e[8] = v1.w;
+        e[9] = xs + 8 < a.W ? __ldg(row + xs + 8) : 0.f;
+      } else {                       // ragged last tile, or rows not 16-byte aligned
+#pragma unroll
+        for (int j = 0; j < 10; ++j) {
+          const int x = xs - 1 + j;
+          e[j] = x >= 0 && x < a.W ? __ldg(row + x) : 0.f;
+        }
+      }
     } else {
 #pragma unroll
       for (int c = 0; c < 10; ++c) e[c] = 0.f;
@@ -424,9 +450,18 @@ __device__ __forceinline__ void wgrad_load_gout(const WgradTcArgs& a, WgradRegs<
     const int idx = tid + k * P::THREADS;
     if (idx < a.Cout * P::PG) {
       const int pg = idx / a.Cout, o = idx - pg * a.Cout;
-      const float* src = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W + x0 + 8 * pg;
-      R.g[k][0] = __ldg(reinterpret_cast<const float4*>(src));
-      R.g[k][1] = __ldg(reinterpret_cast<const float4*>(src + 4));
+      const int xs = x0 + 8 * pg;
+      const float* row = a.gout + (((size_t)b * a.Cout + o) * a.H + y) * a.W;
+      if ((a.W & 3) == 0 && xs + 8 <= a.W) {
+        R.g[k][0] = __ldg(reinterpret_cast<const float4*>(row + xs));
+        R.g[k][1] = __ldg(reinterpret_cast<const float4*>(row + xs + 4));
+      } else {                       // ragged last tile, or rows not 16-byte aligned
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = xs + j < a.W ? __ldg(row + xs + j) : 0.f;
+        R.g[k][0] = make_float4(v[0], v[1], v[2], v[3]);
+        R.g[k][1] = make_float4(v[4], v[5], v[6], v[7]);
+      }
     }
   }
 }
@@ -488,7 +523,7 @@ __global__ void __launch_bounds__(WgradTcT<NP>::THREADS, 1) k_wgrad_tc(WgradTcAr
   const uint32_t tmem = tmem_slot;
   const uint32_t idesc = idesc_bf16(TC_M, NP);
   const uint32_t abase = smem_u32(As), bbase = smem_u32(Bs);
-  const int tiles_x = a.W / TC_M;
+  const int tiles_x = (a.W + TC_M - 1) / TC_M;
   const int RU = a.rows_per_unit;
   const int runs = (a.H + RU - 1) / RU;
   const int nunits = a.B * tiles_x * runs;
@@ -635,7 +670,7 @@ void wgrad_plan(int B, int H, int W, int* grid, int* rows_per_unit) {
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   sms = std::max(sms, 1);
-  const long long strips = (long long)B * (W / TC_M);
+  const long long strips = (long long)B * ((W + TC_M - 1) / TC_M);
   const int ru = (int)std::min<long long>(
       H, std::max(4LL, std::min(32LL, strips * H / std::max(1LL, 4LL * sms))));
   const long long nunits = strips * ((H + ru - 1) / ru);
@@ -791,7 +826,7 @@ __global__ void __launch_bounds__(CONV_THREADS, 2) k_conv3x3_ws(ConvTcArgs a) {
   tc_fence_after();
   const uint32_t tmem = tmem_slot;
   const size_t cs = (size_t)a.H * a.W;
-  const int tiles_x = a.W / TC_M;
+  const int tiles_x = (a.W + TC_M - 1) / TC_M;
   const int RU = a.rows_per_unit;
   const int runs = (a.H + RU - 1) / RU;
   const int nunits = a.B * tiles_x * runs;
@@ -925,7 +960,7 @@ cudaError_t launch_tc(const ConvTcArgs& a, cudaStream_t st) {
   const int slots = per_sm * std::max(sms, 1);
   // rows per unit: about four units per CTA, 4..32 rows (two extra input
   // rows are staged per unit)
-  const long long strips = (long long)a.B * (a.W / TC_M);
+  const long long strips = (long long)a.B * ((a.W + TC_M - 1) / TC_M);
   const long long rows = strips * a.H;
   ConvTcArgs args = a;
   args.rows_per_unit = (int)std::max(4LL, std::min(32LL, rows / std::max(1LL, 4LL * slots)));
@@ -953,7 +988,7 @@ cudaError_t launch_ws(const ConvTcArgs& a, cudaStream_t st) {
   const int slots = per_sm * std::max(sms, 1);
   // rows per unit: about two units per CTA, 8..64 rows (two extra input rows
   // are staged per unit)
-  const long long strips = (long long)a.B * (a.W / TC_M);
+  const long long strips = (long long)a.B * ((a.W + TC_M - 1) / TC_M);
   ConvTcArgs args = a;
   args.rows_per_unit = (int)std::max(8LL, std::min(64LL, strips * a.H / std::max(1LL, 2LL * slots)));
   args.rows_per_unit = std::min(args.rows_per_unit, a.H);
@@ -1002,9 +1037,9 @@ bool tc_tile(int Ci, int Co, int* cg, int* np) {
 cudaError_t dispatch(const ConvTcArgs& a, cudaStream_t st) {
   int cg = 0, np = 0;
   if (!tc_tile(a.Cin, a.Cout, &cg, &np)) return cudaErrorInvalidValue;
+  const bool ws = conv_ws_enabled() && a.W % TC_M == 0;   // the variant takes whole tiles only
 #define SHL_TC(CGV, NPV)                                                                \
-  if (cg == CGV && np == NPV)                                                            \
-    return conv_ws_enabled() ? launch_ws<CGV, NPV>(a, st) : launch_tc<CGV, NPV>(a, st);
+  if (cg == CGV && np == NPV) return ws ? launch_ws<CGV, NPV>(a, st) : launch_tc<CGV, NPV>(a, st);
 #define SHL_TC_WIDE(CGV, NPV) \
   if (cg == CGV && np == NPV) return launch_tc<CGV, NPV>(a, st);
   SHL_TC(2, 16) SHL_TC(2, 32) SHL_TC(2, 48)
@@ -1035,7 +1070,7 @@ extern "C" {
 
 int shl_nn_conv3x3_tc_supported(int Ci, int Co, int H, int W) {
   int cg = 0, np = 0;
-  return tc_tile(Ci, Co, &cg, &np) && H >= 1 && W >= TC_M && W % TC_M == 0;
+  return tc_tile(Ci, Co, &cg, &np) && H >= 1 && W >= 16 && W % 2 == 0;
 }
 
 shl_status shl_nn_conv3x3_forward_tc(const float* in, const float* w, const float* bias,
@@ -1063,7 +1098,7 @@ shl_status shl_nn_conv3x3_backward_data_tc(const float* gout, const float* w, fl
 }
 
 int shl_nn_conv3x3_wgrad_tc_supported(int Ci, int Co, int H, int W) {
-  return Ci >= 1 && 3 * Ci <= 128 && Co >= 1 && Co <= 96 && H >= 1 && W >= TC_M && W % TC_M == 0;
+  return Ci >= 1 && 3 * Ci <= 128 && Co >= 1 && Co <= 96 && H >= 1 && W >= 16 && W % 2 == 0;
 }
 
 size_t shl_nn_conv3x3_backward_weight_tc_workspace_floats(int B, int Ci, int Co, int H, int W) {

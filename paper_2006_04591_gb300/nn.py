@@ -201,7 +201,7 @@ def _groups(n, g):
 
 
 def _tc_width_ok(H, W):
-    return H >= 1 and W >= 128 and W % 128 == 0
+    return H >= 1 and W >= 16 and W % 2 == 0
 
 
 def _axpy(src, dst, alpha=1.0):
@@ -495,7 +495,7 @@ def conv3x3(x, w, b, tc=False):
     weight gradient on the tensor cores (bfloat16 operands, float32
     accumulation) where one call takes the shape, else the float32 kernels;
     tc="grouped" runs every pass on the tensor cores whenever the row width
-    is a multiple of 128, in channel groups for wider layers (measured slower
+    is even (at least 16), in channel groups for wider layers (measured slower
     for the learned primal-dual networks, whose steps are bound by launches)."""
     return _Conv3x3.apply(x, w, b, tc)
 

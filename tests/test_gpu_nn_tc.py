@@ -30,7 +30,11 @@ def _bf(t):
 SHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 16, 16, 3, 384),
           (1, 48, 48, 2, 128), (3, 32, 32, 1, 128), (1, 7, 5, 6, 256),
           (1, 102, 32, 3, 128), (2, 32, 85, 2, 128), (1, 85, 32, 2, 128), (1, 32, 102, 2, 128),
-          (1, 64, 16, 2, 128), (1, 16, 60, 2, 256)]
+          (1, 64, 16, 2, 128), (1, 16, 60, 2, 256),
+          # widths that are not multiples of 128 (ragged last tile) or of 4
+          # (float2 loads): the dual networks' 30 x 182 sinograms and others
+          (2, 7, 32, 30, 182), (1, 32, 5, 4, 182), (1, 16, 16, 3, 200), (1, 8, 32, 2, 130),
+          (1, 32, 32, 5, 64), (1, 4, 16, 3, 18)]
 
 
 @pytest.mark.parametrize("B,Ci,Co,H,W", SHAPES)
@@ -65,7 +69,8 @@ def test_tc_backward_data_matches_rounded_oracle(B, Ci, Co, H, W):
 
 WSHAPES = [(2, 33, 32, 5, 128), (1, 32, 33, 4, 256), (2, 2, 32, 3, 128), (1, 42, 48, 2, 128),
            (3, 32, 16, 1, 128), (1, 7, 5, 6, 256), (1, 32, 85, 3, 128), (2, 16, 96, 2, 128),
-           (1, 42, 60, 2, 256)]
+           (1, 42, 60, 2, 256), (2, 7, 32, 30, 182), (1, 32, 5, 4, 182), (1, 16, 16, 3, 200),
+           (1, 32, 32, 2, 64), (1, 4, 8, 3, 18)]
 
 
 @pytest.mark.parametrize("B,Ci,Co,H,W", WSHAPES)
@@ -87,14 +92,16 @@ def test_tc_weight_gradient_matches_rounded_oracle(B, Ci, Co, H, W):
 def test_tc_rejects_unsupported_shapes():
     from paper_2006_04591_gb300 import nn
     from paper_2006_04591_gb300.shearlet import ShearletError
-    assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 100)
+    assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 181)      # odd width
+    assert not nn.shl_nn_conv3x3_tc_supported(32, 32, 8, 14)       # narrower than 16
     assert not nn.shl_nn_conv3x3_tc_supported(120, 32, 8, 128)     # more than 112 inputs
     assert not nn.shl_nn_conv3x3_tc_supported(64, 64, 8, 128)      # wide on both sides
     assert not nn.shl_nn_conv3x3_tc_supported(48, 80, 8, 128)
     assert not nn.shl_nn_conv3x3_tc_supported(32, 120, 8, 128)
     assert not nn.shl_nn_conv3x3_wgrad_tc_supported(43, 32, 8, 128)
     assert not nn.shl_nn_conv3x3_wgrad_tc_supported(32, 97, 8, 128)
-    x = torch.zeros((1, 32, 8, 100), device="cuda")
+    assert not nn.shl_nn_conv3x3_wgrad_tc_supported(32, 32, 8, 99)
+    x = torch.zeros((1, 32, 8, 101), device="cuda")
     with pytest.raises(ShearletError):
         nn.shl_nn_conv3x3_forward_tc(x, torch.zeros((32, 32, 3, 3), device="cuda"), None,
                                      torch.empty_like(x))
@@ -183,7 +190,8 @@ def test_warp_specialised_conv_matches_rounded_oracle():
 @pytest.mark.parametrize("tc,B,Ci,Co,H,W", [
     ("grouped", 2, 102, 32, 3, 128), ("grouped", 1, 32, 85, 4, 128),
     ("grouped", 1, 102, 85, 2, 256), ("grouped", 2, 7, 32, 3, 256),
-    (True, 2, 102, 32, 3, 128), (True, 1, 32, 85, 4, 128), (True, 2, 85, 32, 2, 128)])
+    (True, 2, 102, 32, 3, 128), (True, 1, 32, 85, 4, 128), (True, 2, 85, 32, 2, 128),
+    (True, 2, 7, 32, 30, 182), ("grouped", 1, 102, 32, 3, 182)])
 def test_wide_tc_conv_autograd_matches_rounded_oracle(tc, B, Ci, Co, H, W):
     # the shearlet-domain primal layers of the learned primal-dual
     # reconstruction (102 -> 32, 32 -> 85): tc=True takes them in one call per
