@@ -299,6 +299,8 @@ def evaluate(net, op, N=128, seed=123):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps-image", type=int, default=None, help="overrides --steps")
+    ap.add_argument("--steps-shearlet", type=int, default=None, help="overrides --steps")
     ap.add_argument("--batch", type=int, default=4)
     ap.add_argument("--out", default=None)
     args = ap.parse_args()
@@ -306,8 +308,11 @@ def main():
     _build.build()
     res = {"size": 128, "angles": 30, "iterations": 10, "n_primal": 5, "n_dual": 5,
            "batch": args.batch, "train_steps": args.steps, "noise": "5% of mean |Rf|"}
+    steps = {"image": args.steps_image or args.steps, "shearlet": args.steps_shearlet or args.steps}
+    res["train_steps"] = steps
     for domain in ("image", "shearlet"):
-        net, op, bank, hist, ts = train(domain, steps=args.steps, batch=args.batch)
+        net, op, bank, hist, ts = train(domain, steps=steps[domain], batch=args.batch,
+                                        log_every=max(100, steps[domain] // 60))
         ev = evaluate(net, op)
         res[domain] = dict(ev, loss=hist, ms_per_train_step=1e3 * float(np.median(ts[5:])),
                            filters=bank.K if bank else None,
