@@ -464,6 +464,10 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   }
   const int S = stage_override > 0 ? stage_override : stage_subbands(b);
   const bool tc = use_tc_dft(b, dtype);
+  // bfloat16 coefficients: the staged half spectra between the column and the
+  // row pass are bfloat16 too (half the staging traffic; the rounding is of
+  // the size of the coefficients' own)
+  const bool s16 = dtype == SHL_BF16 && !tc;
   for (int s0 = 0; s0 < total; s0 += S) {
     const int Sc = std::min(S, total - s0);
     if (tc) {
@@ -471,14 +475,14 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
       e = shl::launch_dec_lines_tc(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
     } else {
       Launch L_("dec_lines", st);
-      e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
+      e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch, s16);
     }
     if (e) return cuda_fail(e, "dec_lines");
     {
       Launch L_("rows_c2r_coeffs", st);
       e = shl::launch_rows_c2r_t(M, dtype == SHL_BF16, Z,
                                  static_cast<char*>(coeffs) + (size_t)s0 * N * M * esz, N, Sc,
-                                 b->dTw, st);
+                                 b->dTw, st, s16);
     }
     if (e) return cuda_fail(e, "rows_c2r_coeffs");
   }

@@ -140,15 +140,18 @@ struct RowsT {
   static constexpr int THREADS = LPC * T;
   static constexpr int Mh = L + 1;
   static constexpr int CPITCH = TR + 2;           // c2r input tile pitch (16-byte rows)
+  static constexpr int CPITCH16 = TR + 2;         // bfloat16 stage: pitch in bfloat162 words (8-byte rows)
   // the transpose tile reuses the line buffers (separated by __syncthreads)
   static constexpr size_t LINES = (size_t)LPC * C::WORDS, TILE = (size_t)Mh * TP;
   static constexpr size_t WORK = sizeof(float2) * (LINES > TILE ? LINES : TILE);
   static constexpr size_t CSTAGE = sizeof(float2) * (size_t)Mh * CPITCH;
+  static constexpr size_t CSTAGE16 = (4 * (size_t)Mh * CPITCH16 + 15) / 16 * 16;
   static constexpr size_t SMEM_CAP = 224 * 1024;
   static constexpr int MINB = M <= 512 ? 2 : 1;    // CTAs per SM the sizes allow
   // twiddles: line stages, split factors exp(-2 pi i p / M), lane bases
   static constexpr size_t TWB = sizeof(float2) * ((size_t)LineTw<L, R>::WORDS + L + LineTwB<L, R>::WORDS);
   static constexpr int CNST = 2 * CSTAGE + WORK + TWB <= SMEM_CAP ? 2 : 1;   // c2r pipeline depth
+  static constexpr int CNST16 = 2 * CSTAGE16 + WORK + TWB <= SMEM_CAP ? 2 : 1;
   static_assert(CSTAGE + WORK + TWB <= SMEM_CAP, "c2r tile does not fit shared memory");
 };
 
@@ -357,42 +360,63 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
 }
 
 struct RowsTC2RArgs {
-  const float2* in;          // [nsub][Mh][N]
+  const void* in;            // [nsub][Mh][N] float2, or bfloat162 (bfloat16 staging)
   void* out;                 // [nsub][N][M]
   const float2* tw;
   int N, nsub;
 };
 
-template <int LOG_M>
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// Stage tile t's TR rows of every kx: 16-byte (float2 staging) or 8-byte
+// (bfloat16 staging, S16) chunks of two rows.
+template <int LOG_M, bool S16 = false>
 __device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, int t, int tid) {
   using P = RowsT<LOG_M>;
   const int tiles_per_sub = a.N / P::TR;
   const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * P::TR;
-  const float2* in = a.in + (size_t)s * P::Mh * a.N + y0;
-  constexpr int CH = P::TR / 2;                       // 16-byte chunks per kx row
+  constexpr int CH = P::TR / 2;                       // two-row chunks per kx row
   if (!SHL_IN((size_t)s * a.N + y0 + P::TR - 1, (size_t)a.nsub * a.N, CHK_C2R_IN)) return;
-  for (int c = tid; c < P::Mh * CH; c += P::THREADS) {
-    const int kx = c / CH, q = c % CH;
-    cp_async16(stage + kx * P::CPITCH + 2 * q, in + (size_t)kx * a.N + 2 * q);
+  if constexpr (S16) {
+    const __nv_bfloat162* in =
+        static_cast<const __nv_bfloat162*>(a.in) + (size_t)s * P::Mh * a.N + y0;
+    __nv_bfloat162* st = reinterpret_cast<__nv_bfloat162*>(stage);
+    for (int c = tid; c < P::Mh * CH; c += P::THREADS) {
+      const int kx = c / CH, q = c % CH;
+      cp_async8(st + kx * P::CPITCH16 + 2 * q, in + (size_t)kx * a.N + 2 * q);
+    }
+  } else {
+    const float2* in = static_cast<const float2*>(a.in) + (size_t)s * P::Mh * a.N + y0;
+    for (int c = tid; c < P::Mh * CH; c += P::THREADS) {
+      const int kx = c / CH, q = c % CH;
+      cp_async16(stage + kx * P::CPITCH + 2 * q, in + (size_t)kx * a.N + 2 * q);
+    }
   }
 }
 
 // C2R of one TR-row tile staged as tile[kx * CPITCH + row]: on return v[u]
 // holds (x[2p], x[2p+1]), p = j + u T, of row r of the tile (lanes j of
 // group r); unnormalised (the 1/(N M) sits in the filter or weight factors).
-template <int LOG_M>
+template <int LOG_M, bool S16 = false>
 __device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* line,
                                                  const float2* twl, const float2* ptw, int r,
                                                  int j, bool valid,
                                                  float2 (&v)[RowsT<LOG_M>::R]) {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, CP = P::CPITCH;
+  constexpr int T = P::T, R = P::R, L = P::L, CP = S16 ? P::CPITCH16 : P::CPITCH;
   const int rr = valid ? r : 0;
+  auto at = [&](int i) -> float2 {
+    if constexpr (S16) return __bfloat1622float2(reinterpret_cast<const __nv_bfloat162*>(tile)[i]);
+    else return tile[i];
+  };
 #pragma unroll
   for (int u = 0; u < R; ++u) {
     const int kk = j + u * T;
-    const float2 A = tile[kk * CP + rr];
-    const float2 B = tile[(L - kk) * CP + rr];
+    const float2 A = at(kk * CP + rr);
+    const float2 B = at((L - kk) * CP + rr);
     const float2 S = make_float2(A.x + B.x, A.y - B.y);
     const float2 D = make_float2(A.x - B.x, A.y + B.y);
     const float2 wd = cmulc(D, split_tw<LOG_M, T>(ptw, ptw + L, j, u));   // D * exp(+2 pi i k / M)
@@ -402,14 +426,14 @@ __device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* lin
 }
 
 // C2R of one staged tile and the store of row r to out + base.
-template <int LOG_M, bool BF16OUT>
+template <int LOG_M, bool BF16OUT, bool S16 = false>
 __device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
                                               const float2* twl, const float2* ptw, void* out,
                                               size_t base, int r, int j, bool valid) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R;
   float2 v[R];
-  c2r_tile_compute<LOG_M>(tile, line, twl, ptw, r, j, valid, v);
+  c2r_tile_compute<LOG_M, S16>(tile, line, twl, ptw, r, j, valid, v);
   if (valid) {
 #pragma unroll
     for (int u = 0; u < R; ++u) {
@@ -425,13 +449,15 @@ __device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
   }
 }
 
-template <int LOG_M, bool BF16OUT>
+// S16: the staged half spectra are bfloat16 (the bfloat16 decomposition).
+template <int LOG_M, bool BF16OUT, bool S16>
 __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_c2r_t(RowsTC2RArgs a) {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, TR = P::TR, NST = P::CNST;
+  constexpr int T = P::T, R = P::R, L = P::L, TR = P::TR, NST = S16 ? P::CNST16 : P::CNST;
+  constexpr size_t SW = (S16 ? P::CSTAGE16 : P::CSTAGE) / sizeof(float2);
   extern __shared__ __align__(16) float2 smem[];
   float2* stages = smem;
-  float2* work = smem + NST * (P::CSTAGE / sizeof(float2));
+  float2* work = smem + NST * SW;
   float2* twl = work + P::WORK / sizeof(float2);
   float2* ptw = twl + LineTw<L, R>::WORDS;
   const int tid = threadIdx.x;
@@ -441,26 +467,26 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
   float2* line = work + (size_t)r * P::C::WORDS;
   const int tiles_per_sub = a.N / TR;
   const int ntiles = a.nsub * tiles_per_sub;
-  constexpr size_t SW = P::CSTAGE / sizeof(float2);
 
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
   LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
-  if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M>(a, stages, blockIdx.x, tid);
+  if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M, S16>(a, stages, blockIdx.x, tid);
   cp_async_commit();
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
     const int tn = NST == 2 ? t + gridDim.x : t;
-    if (tn < ntiles) c2r_issue<LOG_M>(a, stages + ((k + 1) % NST) * SW, tn, tid);
+    if (tn < ntiles) c2r_issue<LOG_M, S16>(a, stages + ((k + 1) % NST) * SW, tn, tid);
     cp_async_commit();
     if (NST == 2) cp_async_wait1(); else cp_async_wait0();
     __syncthreads();
     const float2* tile = stages + (k % NST) * SW;
     const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
 
-    c2r_tile_body<LOG_M, BF16OUT>(tile, line, twl, ptw, a.out, ((size_t)s * a.N + y0 + rr) * P::M, r,
-                                  j, valid && SHL_IN((size_t)s * a.N + y0 + rr, (size_t)a.nsub * a.N,
-                                                     CHK_C2R_OUT));
+    c2r_tile_body<LOG_M, BF16OUT, S16>(tile, line, twl, ptw, a.out,
+                                       ((size_t)s * a.N + y0 + rr) * P::M, r, j,
+                                       valid && SHL_IN((size_t)s * a.N + y0 + rr,
+                                                       (size_t)a.nsub * a.N, CHK_C2R_OUT));
     __syncthreads();                       // stage reuse
   }
   cp_async_wait0();
@@ -545,13 +571,14 @@ struct LinesT {
 
 struct LinesArgs {
   float2* data;              // FWD: [nlines][N] in place; DEC: image spectra [B][Mh][N]
-  float2* out;               // DEC: staging [S][Mh][N]
+  void* out;                 // DEC: staging [S][Mh][N], float2 (or bfloat162 with s16)
   const float* G;            // [K][Mh][N]
   const float* invW;         // [Mh][N] or null
   const float2* tw;
   float scale;
   int Mh, K, s0, nlines;
   int nimg;                  // image planes of data (checked build)
+  int s16;                   // DEC: bfloat16 staging (the bfloat16 decomposition)
 };
 
 template <int LOG_N>
@@ -585,8 +612,8 @@ constexpr int DEC_FPG = 4;
 
 // One lane group: kx line `kx` of the chunk subbands sl0..sl1-1 (global
 // subband s0 + sl, image s / K, filter s mod K) into out[sl][kx][:].
-template <int LOG_N>
-__device__ __forceinline__ void dec_group(const float2* X, float2* out, const float* Gall,
+template <int LOG_N, bool S16 = false>
+__device__ __forceinline__ void dec_group(const float2* X, void* out, const float* Gall,
                                           const float* invW, float scale, int Mh, int K, int s0,
                                           int sl0, int sl1, int kx, float2* line, const float2* twl,
                                           int j, int g, int nimg = 0x7fffffff,
@@ -631,15 +658,21 @@ __device__ __forceinline__ void dec_group(const float2* X, float2* out, const fl
       v[u] = cscale(Xl[u], gv);
     }
     line_fft_any<N, R, +1>(v, line, j, 1 + g, twl, twl + LineTw<N, R>::WORDS);
-    float2* o = out + ((size_t)sl * Mh + kx) * N;
     if (SHL_IN((size_t)sl * Mh + kx, (size_t)nstage * Mh, CHK_DEC_OUT)) {
+      if constexpr (S16) {
+        __nv_bfloat162* o = static_cast<__nv_bfloat162*>(out) + ((size_t)sl * Mh + kx) * N;
 #pragma unroll
-      for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
+        for (int u = 0; u < R; ++u) o[j + u * T] = __floats2bfloat162_rn(v[u].x, v[u].y);
+      } else {
+        float2* o = static_cast<float2*>(out) + ((size_t)sl * Mh + kx) * N;
+#pragma unroll
+        for (int u = 0; u < R; ++u) o[j + u * T] = v[u];
+      }
     }
   }
 }
 
-template <int LOG_N>
+template <int LOG_N, bool S16>
 __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   using P = LinesT<LOG_N>;
   constexpr int T = P::T, R = P::R, N = P::N;
@@ -656,8 +689,8 @@ __global__ void __launch_bounds__(256) k_dec_lines(LinesArgs a) {
   for (int q = blockIdx.x * P::NG + g; q < items; q += gridDim.x * P::NG) {
     const int m = q / a.Mh, kx = q - m * a.Mh;
     const int sl0 = m * DEC_FPG, sl1 = min(S, sl0 + DEC_FPG);
-    dec_group<LOG_N>(a.data, a.out, a.G, a.invW, a.scale, a.Mh, a.K, a.s0, sl0, sl1, kx, line, twl,
-                     j, g, a.nimg, S);
+    dec_group<LOG_N, S16>(a.data, a.out, a.G, a.invW, a.scale, a.Mh, a.K, a.s0, sl0, sl1, kx, line,
+                          twl, j, g, a.nimg, S);
   }
 }
 
@@ -827,7 +860,7 @@ __device__ __noinline__ bool pipe_wait(const unsigned* flag, unsigned target) {
     if (ld_acquire_u32(flag) >= target) return true;
     if (*(volatile unsigned*)&g_pipe_err) return false;
     if (spin >= PIPE_SPIN_LIMIT) {
-      atomicOr(&g_pipe_err, 1u);
+      atomicOr(&g_pipe_err, WAIT_PIPE);
       return false;
     }
     if (spin > 32) __nanosleep(128);
@@ -1010,21 +1043,22 @@ static cudaError_t r2c_t(InMode mode, bool th, const RowsTArgs& a, cudaStream_t 
 }
 
 template <int LOG_M>
-static cudaError_t c2r_t(bool bf16, const RowsTC2RArgs& a, cudaStream_t st) {
+static cudaError_t c2r_t(bool bf16, bool s16, const RowsTC2RArgs& a, cudaStream_t st) {
   using P = RowsT<LOG_M>;
   const int ntiles = a.nsub * (a.N / P::TR);
   if (ntiles == 0) return cudaSuccess;
   const int grid = std::min(ntiles, sm_count() * P::MINB);
-  const size_t sm = P::CNST * P::CSTAGE + P::WORK + P::TWB;
+  const size_t sm = (s16 ? P::CNST16 * P::CSTAGE16 : P::CNST * P::CSTAGE) + P::WORK + P::TWB;
   cudaError_t e;
-  if (bf16) {
-    if ((e = prep(k_rows_c2r_t<LOG_M, true>, sm))) return e;
-    k_rows_c2r_t<LOG_M, true><<<grid, P::THREADS, sm, st>>>(a);
-  } else {
-    if ((e = prep(k_rows_c2r_t<LOG_M, false>, sm))) return e;
-    k_rows_c2r_t<LOG_M, false><<<grid, P::THREADS, sm, st>>>(a);
+#define SHL_C2R(B, S)                                                   \
+  if (bf16 == B && s16 == S) {                                          \
+    if ((e = prep(k_rows_c2r_t<LOG_M, B, S>, sm))) return e;            \
+    k_rows_c2r_t<LOG_M, B, S><<<grid, P::THREADS, sm, st>>>(a);         \
+    return cudaGetLastError();                                          \
   }
-  return cudaGetLastError();
+  SHL_C2R(true, true) SHL_C2R(true, false) SHL_C2R(false, false)
+#undef SHL_C2R
+  return cudaErrorInvalidValue;                 // bfloat16 staging only with bfloat16 output
 }
 
 template <int LOG_M>
@@ -1055,14 +1089,18 @@ static cudaError_t lines_t(int mode, const LinesArgs& a, const RecLinesArgs& ra,
     if (mode == 0) {
       if ((e = prep(k_lines_fwd<LOG_N>, sm))) return e;
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lines_fwd<LOG_N>, P::THREADS, sm);
+    } else if (a.s16) {
+      if ((e = prep(k_dec_lines<LOG_N, true>, sm))) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_lines<LOG_N, true>, P::THREADS, sm);
     } else {
-      if ((e = prep(k_dec_lines<LOG_N>, sm))) return e;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_lines<LOG_N>, P::THREADS, sm);
+      if ((e = prep(k_dec_lines<LOG_N, false>, sm))) return e;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dec_lines<LOG_N, false>, P::THREADS, sm);
     }
     if (e) return e;
     const int grid = std::max(1, std::min((work + P::NG - 1) / P::NG, std::max(per_sm, 1) * sm_count()));
     if (mode == 0) k_lines_fwd<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
-    else k_dec_lines<LOG_N><<<grid, P::THREADS, sm, st>>>(a);
+    else if (a.s16) k_dec_lines<LOG_N, true><<<grid, P::THREADS, sm, st>>>(a);
+    else k_dec_lines<LOG_N, false><<<grid, P::THREADS, sm, st>>>(a);
   } else {
     const size_t sm = P::SMEM_LINES + sizeof(float2) * (size_t)P::NG * P::N + P::TWB;
     if ((e = prep(k_rec_lines<LOG_N>, sm))) return e;
@@ -1093,10 +1131,10 @@ cudaError_t launch_rows_r2c_t(int M, InMode mode, bool thresh, const void* in, c
 #undef CALL
 }
 
-cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int N, int nsub,
-                              const float2* tw, cudaStream_t st) {
+cudaError_t launch_rows_c2r_t(int M, bool bf16, const void* in, void* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st, bool s16) {
   RowsTC2RArgs a{in, out, tw, N, nsub};
-#define CALL(X) c2r_t<X>(bf16, a, st)
+#define CALL(X) c2r_t<X>(bf16, s16, a, st)
   SHL_SWITCH_LOG(ilog2(M), CALL)
 #undef CALL
 }
@@ -1118,12 +1156,13 @@ cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, 
 #undef CALL
 }
 
-cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
+cudaError_t launch_dec_lines(int N, const float2* X, void* out, const float* G, const float* invW,
                              float scale, int Mh, int K, int s0, int S, const float2* tw,
-                             cudaStream_t st, int nimg) {
+                             cudaStream_t st, int nimg, bool s16) {
   LinesArgs a{};
   a.data = const_cast<float2*>(X); a.out = out; a.G = G; a.invW = invW; a.tw = tw;
   a.scale = scale; a.Mh = Mh; a.K = K; a.s0 = s0; a.nlines = S * Mh; a.nimg = nimg;
+  a.s16 = s16 ? 1 : 0;
   RecLinesArgs ra{};
 #define CALL(X) lines_t<X>(1, a, ra, 0, st)
   SHL_SWITCH_LOG(ilog2(N), CALL)

@@ -26,17 +26,19 @@ enum InMode : int {
 cudaError_t launch_rows_r2c_t(int M, InMode mode, bool thresh, const void* in, const uint8_t* mask,
                               const float* fest, const float* th, float2* out, int N, int nsub,
                               const float2* tw, cudaStream_t st);
-cudaError_t launch_rows_c2r_t(int M, bool bf16, const float2* in, void* out, int N, int nsub,
-                              const float2* tw, cudaStream_t st);
+// s16: the staged planes are bfloat16 (bfloat16 output only).
+cudaError_t launch_rows_c2r_t(int M, bool bf16, const void* in, void* out, int N, int nsub,
+                              const float2* tw, cudaStream_t st, bool s16 = false);
 // In place on [nsub][Mh][N] half spectra: C2R rows -> zero |c| < thresh[s]
 // -> R2C rows (the fused threshold of the denoise / IHT step).
 cudaError_t launch_rows_shrink_t(int M, float2* z, const float* thresh, int N, int nsub,
                                  const float2* tw, cudaStream_t st);
 cudaError_t launch_lines_fwd(int N, float2* data, int nlines, const float2* tw, cudaStream_t st);
-// nimg: image planes of X / acc (bounds of the checked build).
-cudaError_t launch_dec_lines(int N, const float2* X, float2* out, const float* G, const float* invW,
+// nimg: image planes of X / acc (bounds of the checked build); s16: write
+// the staged planes as bfloat16 (the bfloat16 decomposition).
+cudaError_t launch_dec_lines(int N, const float2* X, void* out, const float* G, const float* invW,
                              float scale, int Mh, int K, int s0, int S, const float2* tw,
-                             cudaStream_t st, int nimg);
+                             cudaStream_t st, int nimg, bool s16 = false);
 cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const float* G,
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
                              const float2* tw, cudaStream_t st, int nimg);
