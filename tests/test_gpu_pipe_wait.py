@@ -1,5 +1,5 @@
 """The pipelined decomposition (opt-in, SHL_PIPE=1) against the oracle and,
-bit for bit, against the two-launch path; and its waits are bounded: with every ROW wait made
+bit for bit with float32 coefficients, against the two-launch path; and its waits are bounded: with every ROW wait made
 unsatisfiable (SHL_PIPE_STALL_TEST=1, a count that no item reaches), the
 launch ends by itself, shl_sync reports SHL_ETIMEOUT, and the same process
 then decomposes correctly.  Runs in a child process so that the variable
@@ -69,11 +69,21 @@ PARITY = textwrap.dedent("""
                               (torch.float32, True, 1e-5)]:
             c = bank.decompose(xt, dtype=dt, dual=dual)
             assert S.lib().shl_sync(None) == 0
-            # the two-launch path with a small staging area (same arithmetic)
+            # the two-launch path with a small staging area: the same
+            # arithmetic for float32 coefficients (bfloat16 coefficients: it
+            # stages the half spectra in bfloat16, the pipelined path in
+            # float32, so both are held to the oracle below instead)
             c2 = torch.empty_like(c)
             S.shl_decompose_noalloc(bank.handle, xt, B, c2, S._dtype_code(dt),
                                     S.SHL_DUAL_WEIGHTED if dual else 0)
-            assert torch.equal(c, c2), (rows, cols, J, B, dt, dual)
+            if dt == torch.float32:
+                assert torch.equal(c, c2), (rows, cols, J, B, dt, dual)
+            else:
+                w16, _ = OT.decompose_batch(x, ref["psi_hat"], dual=dual)
+                g16 = c2.float().cpu().numpy()
+                for b in range(B):
+                    e16 = np.abs(g16[b] - w16[b]).max() / np.abs(w16[b]).max()
+                    assert e16 <= tol, (rows, cols, J, b, dt, dual, e16)
             want, _ = OT.decompose_batch(x, ref["psi_hat"], dual=dual)
             got = c.float().cpu().numpy()
             for b in range(B):
