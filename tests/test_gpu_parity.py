@@ -296,9 +296,12 @@ def test_max_size_2048():
     x = _images(1, 2048, 2048, 123)
     xt = torch.from_numpy(x).cuda()
     c = bank.decompose(xt)
+    c16 = bank.decompose(xt, dtype=torch.bfloat16)     # bfloat16 staging at 2048-long rows
     for i in (0, 5, 16):
         want = OT.decompose(x[0], ref["psi_hat"][i:i + 1]).real[0]
         assert _rel(c[0, i].cpu().numpy(), want) <= TOL32, i
+        assert _rel(c16[0, i].float().cpu().numpy(), want) <= TOL16, i
+    del c16
     r = bank.reconstruct(c)
     assert (r - xt).abs().max().item() <= TOL32 * xt.abs().max().item()
     w = torch.randn(c.shape, generator=torch.Generator().manual_seed(3)).cuda()
