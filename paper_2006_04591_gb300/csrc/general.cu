@@ -401,7 +401,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_rows(const RowArgs a) {
 }
 
 // --------------------------------------------------------------- columns
-enum ColKind : int { COL_FWD = 0, COL_DEC = 1, COL_REC = 2 };
+enum ColKind : int { COL_FWD = 0, COL_DEC = 1, COL_REC = 2, COL_FIN = 3 };
 
 struct ColArgs {
   LinePlan pn;               // columns: length N
@@ -411,7 +411,27 @@ struct ColArgs {
   const void* G;             // float [K][N][W] or float2 [K][N][W]
   const float* invW;         // [N][W] or null
   int W, K, s0, S, C, pitch, cplx;   // W = M/2 + 1 stored columns
+  int groups;                // COL_REC / COL_FIN: subband groups per image (blockIdx.z)
 };
+
+// Subbands [sa, sb) of image b in the chunk s0 .. s0+S-1, and their group g
+// of `groups`: [lo, hi) (possibly empty).
+struct RecRange {
+  int b, sa, sb, lo, hi;
+  bool first, last;
+};
+__device__ __forceinline__ RecRange rec_range(const ColArgs& a, int img, int g) {
+  RecRange r;
+  r.b = a.s0 / a.K + img;
+  r.sa = max(a.s0, r.b * a.K);
+  r.sb = min(a.s0 + a.S, (r.b + 1) * a.K);
+  r.first = r.sa == r.b * a.K;
+  r.last = r.sb == (r.b + 1) * a.K;
+  const int n = r.sb - r.sa;
+  r.lo = r.sa + (g * n) / a.groups;
+  r.hi = r.sa + ((g + 1) * n) / a.groups;
+  return r;
+}
 
 __device__ __forceinline__ float2 filter_at(const ColArgs& a, int i, size_t e, size_t plane) {
   if (a.cplx) return __ldg(static_cast<const float2*>(a.G) + (size_t)i * plane + e);
@@ -465,23 +485,17 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols(const ColArgs a) {
       const int y = qdiv(idx, rC), c = idx - y * C;
       Ts[(size_t)y * W + col0 + c] = conj2(res[c * a.pitch + y]);
     }
-  } else {
-    const int b = a.s0 / a.K + blockIdx.y;
-    const int sa = max(a.s0, b * a.K), sb = min(a.s0 + a.S, (b + 1) * a.K);
-    const bool first = sa == b * a.K, last = sb == (b + 1) * a.K;
-    float2* Ab = a.A + (size_t)b * plane;
+  } else if constexpr (KIND == COL_REC) {
+    // group blockIdx.z of image blockIdx.y: its subbands' column DFTs times
+    // conj(G_i), summed in order of i in registers, written over the
+    // columns of the group's first staging plane (which only this CTA reads)
+    const RecRange r = rec_range(a, blockIdx.y, blockIdx.z);
+    if (r.lo >= r.hi) return;
     float2 acc[COL_ACC];
 #pragma unroll
-    for (int u = 0; u < COL_ACC; ++u) {
-      const int idx = threadIdx.x + u * COL_THREADS;
-      acc[u] = make_float2(0.f, 0.f);
-      if (!first && idx < NC) {
-        const int y = qdiv(idx, rC), c = idx - y * C;
-        acc[u] = Ab[(size_t)y * W + col0 + c];
-      }
-    }
-    for (int s = sa; s < sb; ++s) {
-      const int i = s - b * a.K;
+    for (int u = 0; u < COL_ACC; ++u) acc[u] = make_float2(0.f, 0.f);
+    for (int s = r.lo; s < r.hi; ++s) {
+      const int i = s - r.b * a.K;
       const float2* Ts = a.T + (size_t)(s - a.s0) * plane;
       for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
         const int y = qdiv(idx, rC), c = idx - y * C;
@@ -501,26 +515,46 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols(const ColArgs a) {
       }
       __syncthreads();
     }
+    float2* part = a.T + (size_t)(r.lo - a.s0) * plane;
 #pragma unroll
     for (int u = 0; u < COL_ACC; ++u) {
       const int idx = threadIdx.x + u * COL_THREADS;
       if (idx < NC) {
         const int y = qdiv(idx, rC), c = idx - y * C;
-        const size_t e = (size_t)y * W + col0 + c;
-        if (!last) {
-          Ab[e] = acc[u];
-        } else {
-          float2 v = acc[u];
-          if (a.invW) {
-            const float w = __ldg(a.invW + e);
-            v.x *= w;
-            v.y *= w;
-          }
-          buf[c * a.pitch + y] = conj2(v);
-        }
+        part[(size_t)y * W + col0 + c] = acc[u];
       }
     }
-    if (!last) return;
+  } else {
+    // COL_FIN, image blockIdx.y: acc = (partial sum in A_b unless the chunk
+    // holds the image's first subband) + the groups' partials in group
+    // order; on the image's last subband acc * 1/W is inverse column
+    // transformed into A_b, else stored there as the new partial sum
+    const RecRange r0 = rec_range(a, blockIdx.y, 0);
+    float2* Ab = a.A + (size_t)r0.b * plane;
+    for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
+      const int y = qdiv(idx, rC), c = idx - y * C;
+      const size_t e = (size_t)y * W + col0 + c;
+      float2 v = r0.first ? make_float2(0.f, 0.f) : Ab[e];
+      for (int g = 0; g < a.groups; ++g) {
+        const RecRange r = rec_range(a, blockIdx.y, g);
+        if (r.lo < r.hi) {
+          const float2 t = a.T[(size_t)(r.lo - a.s0) * plane + e];
+          v.x += t.x;
+          v.y += t.y;
+        }
+      }
+      if (!r0.last) {
+        Ab[e] = v;
+      } else {
+        if (a.invW) {
+          const float w = __ldg(a.invW + e);
+          v.x *= w;
+          v.y *= w;
+        }
+        buf[c * a.pitch + y] = conj2(v);
+      }
+    }
+    if (!r0.last) return;
     float2* res = line_dft(buf, alt, C, a.pitch, p);
     for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
       const int y = qdiv(idx, rC), c = idx - y * C;
@@ -705,15 +739,29 @@ cudaError_t launch_cols_dec(const LinePlan& pn, const float2* X, float2* T, cons
   return launch(k_cols<COL_DEC>, dim3((W + a.C - 1) / a.C, S), COL_THREADS, smem, st, a);
 }
 
-cudaError_t launch_cols_rec(const LinePlan& pn, const float2* T, float2* A, const void* G,
+cudaError_t launch_cols_rec(const LinePlan& pn, float2* T, float2* A, const void* G,
                             bool cplx, const float* invW, int W, int K, int s0, int S,
                             cudaStream_t st) {
   ColArgs a{};
-  a.pn = pn; a.T = const_cast<float2*>(T); a.A = A; a.G = G; a.cplx = cplx; a.invW = invW;
+  a.pn = pn; a.T = T; a.A = A; a.G = G; a.cplx = cplx; a.invW = invW;
   a.W = W; a.K = K; a.s0 = s0; a.S = S; a.C = col_lines(pn, W); a.pitch = pn.P + 1;
   const int nimg = S > 0 ? (s0 + S - 1) / K - s0 / K + 1 : 0;
   const size_t smem = 2 * (size_t)a.C * a.pitch * sizeof(float2);
-  return launch(k_cols<COL_REC>, dim3((W + a.C - 1) / a.C, nimg), COL_THREADS, smem, st, a);
+  const unsigned cb = (unsigned)((W + a.C - 1) / a.C);
+  // subband groups per image: about four waves of CTAs (smem-bound residency)
+  // with at least ceil(K / 16) subbands a group, so that one image's K
+  // transforms are spread over the GPU instead of running in one CTA
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long per_sm = std::max<long long>(1, (228 * 1024) / (long long)(smem + 1024));
+  const long long want = 4LL * std::max(sms, 1) * per_sm;
+  const long long base = std::max<long long>(1, (long long)cb * nimg);
+  a.groups = (int)std::max<long long>(1, std::min<long long>({(want + base - 1) / base, 16,
+                                                              std::min(S, K)}));
+  cudaError_t e = launch(k_cols<COL_REC>, dim3(cb, nimg, a.groups), COL_THREADS, smem, st, a);
+  if (e) return e;
+  return launch(k_cols<COL_FIN>, dim3(cb, nimg), COL_THREADS, smem, st, a);
 }
 
 }  // namespace gen

@@ -76,19 +76,22 @@ cudaError_t launch_rows_shrink(const LinePlan& pm, float2* z, const float* thres
 //   cols_fwd: in-place forward column DFT of nplanes planes.
 //   cols_dec: T[s - s0] = inverse column DFT of G_i * X_b [* 1/W] for the
 //             subbands s = s0 .. s0+S-1 (b = s / K, i = s % K).
-//   cols_rec: for each image b with subbands in s0 .. s0+S-1:
-//             acc = (partial sum in A_b unless the chunk holds the image's
-//             first subband) + sum_i conj(G_i) * column DFT(T[s - s0]) in
-//             order of i; on the image's last subband acc is multiplied by
-//             1/W (when invW) and inverse column transformed into A_b, else
-//             stored there as the new partial sum.
+//   cols_rec: for each image b with subbands in s0 .. s0+S-1, split into
+//             groups of consecutive subbands (one CTA per column block,
+//             image and group): the group's sum_i conj(G_i) * column
+//             DFT(T[s - s0]) in order of i, written over its first staging
+//             plane; then acc = (partial sum in A_b unless the chunk holds
+//             the image's first subband) + the group sums in group order; on
+//             the image's last subband acc is multiplied by 1/W (when invW)
+//             and inverse column transformed into A_b, else stored there as
+//             the new partial sum.  T is overwritten.
 // G is float [K][N][W] (real spectra) or float2 [K][N][W] (complex), 1/W
 // float [N][W]: the columns kx = 0..M/2 of the natural-order tables.
 cudaError_t launch_cols_fwd(const LinePlan& pn, float2* X, int W, int nplanes, cudaStream_t st);
 cudaError_t launch_cols_dec(const LinePlan& pn, const float2* X, float2* T, const void* G,
                             bool cplx, const float* invW, int W, int K, int s0, int S,
                             cudaStream_t st);
-cudaError_t launch_cols_rec(const LinePlan& pn, const float2* T, float2* A, const void* G,
+cudaError_t launch_cols_rec(const LinePlan& pn, float2* T, float2* A, const void* G,
                             bool cplx, const float* invW, int W, int K, int s0, int S,
                             cudaStream_t st);
 
