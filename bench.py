@@ -93,6 +93,19 @@ def _profiled_traffic(kernel):
         return None
 
 
+def _e2e_block(units_per_step, io_bytes, variants):
+    """The end-to-end figure: the fastest of the measured ways of running a
+    step from pinned host images to pinned host results through the public
+    API (each step copies or reads its inputs and results over the
+    CPU-GPU link inside the timed region), with every variant listed."""
+    best = min(variants, key=lambda v: v[0])
+    return {"value": units_per_step / best[0], "unit": UNIT,
+            "h2d_bytes_per_step": io_bytes, "d2h_bytes_per_step": io_bytes,
+            "transfer": best[1], "max_rel_err": best[2],
+            "variants": [{"value": units_per_step / t, "unit": UNIT, "ms_per_step": t * 1e3,
+                          "transfer": d} for t, d, _ in variants]}
+
+
 def kernel_alg_bytes(name, B, K, N, M, s=4):
     """Algorithmic HBM bytes one step's launches of kernel `name` move
     (images, coefficients, filter and 1/W half spectra; no intermediates)."""
@@ -393,9 +406,40 @@ def run_gpu(args):
         bank.reconstruct(coeffs, out=xr, ws=ws_r)
         outh.copy_(xr, non_blocking=True)
 
+    # the same calls pipelined over two streams, one half batch each: one
+    # half's host-to-device copy and device-to-host read overlap the other
+    # half's transforms
+    halves = [(0, B // 2), (B // 2, B)]
+    side = [torch.cuda.Stream(dev) for _ in halves]
+    ws_h = [(bank.workspace(S.SHL_OP_DECOMPOSE, hb - ha), bank.workspace(S.SHL_OP_RECONSTRUCT, hb - ha))
+            for ha, hb in halves]
+    xd_h = [torch.empty((hb - ha, N, N), dtype=torch.float32, device=dev) for ha, hb in halves]
+
+    def e2e_pipe_step():
+        for (ha, hb), s, (wd, wr), xd in zip(halves, side, ws_h, xd_h):
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                xd.copy_(xh[ha:hb], non_blocking=True)
+                bank.decompose(xd, out=coeffs[ha:hb], ws=wd)
+                bank.reconstruct(coeffs[ha:hb], out=xr[ha:hb], ws=wr)
+                outh[ha:hb].copy_(xr[ha:hb], non_blocking=True)
+        for s in side:
+            stream.wait_stream(s)
+
+    def e2e_pipe_mapped_step():
+        for (ha, hb), s, (wd, wr) in zip(halves, side, ws_h):
+            s.wait_stream(stream)
+            with torch.cuda.stream(s):
+                bank.decompose(xh[ha:hb], out=coeffs[ha:hb], ws=wd)
+                bank.reconstruct(coeffs[ha:hb], out=outh[ha:hb], ws=wr)
+        for s in side:
+            stream.wait_stream(s)
+
     for _ in range(3):
         e2e_step()
         e2e_copy_step()
+        e2e_pipe_step()
+        e2e_pipe_mapped_step()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -406,6 +450,17 @@ def run_gpu(args):
         dist.barrier()
     copy_times = timed(e2e_copy_step, args.steps)
     t_copy = reduce_max_time(sum(copy_times) / len(copy_times) / 1e3, dist if world > 1 else None, dev)
+    copy_err = float(np.abs(outh.numpy() - x_host).max() / np.abs(x_host).max())
+    if world > 1:
+        dist.barrier()
+    pipe_times = timed(e2e_pipe_step, args.steps)
+    t_pipe = reduce_max_time(sum(pipe_times) / len(pipe_times) / 1e3, dist if world > 1 else None, dev)
+    pipe_err = float(np.abs(outh.numpy() - x_host).max() / np.abs(x_host).max())
+    if world > 1:
+        dist.barrier()
+    pm_times = timed(e2e_pipe_mapped_step, args.steps)
+    t_pm = reduce_max_time(sum(pm_times) / len(pm_times) / 1e3, dist if world > 1 else None, dev)
+    pm_err = float(np.abs(outh.numpy() - x_host).max() / np.abs(x_host).max())
     if world > 1:
         dist.barrier()
 
@@ -476,13 +531,14 @@ def run_gpu(args):
         "kernels": {k: {"launches_per_step": v["launches"] / args.steps,
                         "ms_per_step": v["ms"] / args.steps} for k, v in prof.items()},
         "profiled_ms_per_step": t_prof * 1e3,
-        "e2e": {"value": coeffs_per_step / t_e2e, "unit": UNIT,
-                "h2d_bytes_per_step": B * N * N * 4, "d2h_bytes_per_step": B * N * N * 4,
-                "transfer": "pinned host images read and written by the first and last "
-                            "kernels over the CPU-GPU link",
-                "max_rel_err": e2e_err,
-                "explicit_copies": {"value": coeffs_per_step / t_copy, "unit": UNIT,
-                                    "transfer": "cudaMemcpyAsync H2D / D2H around the calls"}},
+        "e2e": _e2e_block(coeffs_per_step, B * N * N * 4, [
+            (t_e2e, "pinned host images read and written by the first and last kernels over "
+                    "the CPU-GPU link", e2e_err),
+            (t_copy, "cudaMemcpyAsync H2D / D2H around the calls", copy_err),
+            (t_pipe, "two streams, one half batch each: H2D copy, decompose, reconstruct, D2H "
+                     "copy, the halves overlapping", pipe_err),
+            (t_pm, "two streams, one half batch each, the kernels reading and writing the "
+                   "pinned host images, the halves overlapping", pm_err)]),
         "bf16": bf16_block,
         "gpu_launches": launches,
         "clocks": clock_info,
