@@ -177,11 +177,26 @@ __host__ __device__ constexpr size_t r2c_stage_bytes() {
 }
 // r2c pipeline depth: 2 (double-buffered), 1, or 0 (inputs read straight
 // from global memory when even one staged tile does not fit).
+// Three CTAs per SM (24 warps) where one staged tile, the work buffers and
+// the twiddles fit a third of the SM's shared memory and the input is not
+// the masked triple: one stage, refilled as soon as its rows are in
+// registers, so the next tile's copy still overlaps the current transform.
+template <int LOG_M, int INM>
+__host__ __device__ constexpr bool r2c_occ3() {
+  using P = RowsT<LOG_M>;
+  return INM != IN_MASKED && 3 * (r2c_stage_bytes<LOG_M, INM>() + P::WORK + P::TWB + 1024 + 64) <=
+                                 228 * 1024;
+}
 template <int LOG_M, int INM>
 __host__ __device__ constexpr int r2c_nst() {
   using P = RowsT<LOG_M>;
   constexpr size_t SB = r2c_stage_bytes<LOG_M, INM>(), REST = P::WORK + P::TWB;
+  if (r2c_occ3<LOG_M, INM>()) return 1;
   return 2 * SB + REST <= P::SMEM_CAP ? 2 : (SB + REST <= P::SMEM_CAP ? 1 : 0);
+}
+template <int LOG_M, int INM>
+__host__ __device__ constexpr int r2c_minb() {
+  return r2c_occ3<LOG_M, INM>() ? 3 : RowsT<LOG_M>::MINB;
 }
 
 // Thread 0: start the bulk copies of tile t into `stage`, completing on
@@ -258,12 +273,13 @@ __device__ __forceinline__ void r2c_tile_finish(float2 (&v)[RowsT<LOG_M>::R], fl
 }
 
 template <int LOG_M, int INM, bool THRESH>
-__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_r2c_t(RowsTArgs a) {
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, (r2c_minb<LOG_M, INM>())) k_rows_r2c_t(RowsTArgs a) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, Mh = P::Mh, M = P::M;
   constexpr int TR = P::TR;
   constexpr size_t SB = r2c_stage_bytes<LOG_M, INM>();
   constexpr int NST = r2c_nst<LOG_M, INM>();
+  constexpr bool EARLY = r2c_occ3<LOG_M, INM>();   // one stage, refilled after the read
   extern __shared__ __align__(16) float2 smem[];
   char* stages = reinterpret_cast<char*>(smem);
   float2* work = reinterpret_cast<float2*>(stages + (size_t)NST * SB);
@@ -287,12 +303,22 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
   LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
   __syncthreads();
-  if (NST == 2 && tid == 0 && blockIdx.x < ntiles)
+  if ((NST == 2 || EARLY) && tid == 0 && blockIdx.x < ntiles)
     r2c_issue<LOG_M, INM>(a, stages, blockIdx.x, &full[0]);
   int k = 0;
-  int pending = NST == 2 && blockIdx.x < ntiles ? 1 : 0;    // copies issued, not yet waited on
+  int pending = (NST == 2 || EARLY) && blockIdx.x < ntiles ? 1 : 0;   // copies issued, not waited on
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
-    if constexpr (NST > 0) {
+    if constexpr (EARLY) {
+      const bool ok = mbar_wait_bounded(&full[0], k & 1);     // tile k, the stage's k-th use
+      --pending;
+      if (__syncthreads_or(!ok)) {
+        if (tid == 0) {
+          atomicOr(&g_pipe_err, WAIT_TILE);
+          mbar_wait_bounded(&full[0], k & 1);   // the copy that ran out: let it land
+        }
+        return;
+      }
+    } else if constexpr (NST > 0) {
       const int tn = NST == 2 ? t + gridDim.x : t;
       if (tn < ntiles) {
         if (tid == 0) r2c_issue<LOG_M, INM>(a, stages + ((k + 1) % NST) * SB, tn, &full[(k + 1) % NST]);
@@ -353,6 +379,15 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
       }
       v[u] = valid ? z : make_float2(0.f, 0.f);
     }
+    if constexpr (EARLY) {
+      // the stage is in registers: refill it with the next tile now
+      __syncthreads();
+      const int tn = t + gridDim.x;
+      if (tn < ntiles) {
+        if (tid == 0) r2c_issue<LOG_M, INM>(a, stages, tn, &full[0]);
+        ++pending;
+      }
+    }
 
     r2c_tile_finish<LOG_M>(v, line, tile, twl, ptw, a.out + (size_t)s * Mh * a.N + y0, a.N, r, j,
                            valid, tid, tile_ok);    // ends with a barrier: tile and stage reusable
@@ -400,11 +435,11 @@ __device__ __forceinline__ void c2r_issue(const RowsTC2RArgs& a, float2* stage, 
 // C2R of one TR-row tile staged as tile[kx * CPITCH + row]: on return v[u]
 // holds (x[2p], x[2p+1]), p = j + u T, of row r of the tile (lanes j of
 // group r); unnormalised (the 1/(N M) sits in the filter or weight factors).
+// The split of row r of the staged tile (reads the stage, leaves v[u] =
+// Z[j + u T] of the line before its inverse FFT).
 template <int LOG_M, bool S16 = false>
-__device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* line,
-                                                 const float2* twl, const float2* ptw, int r,
-                                                 int j, bool valid,
-                                                 float2 (&v)[RowsT<LOG_M>::R]) {
+__device__ __forceinline__ void c2r_tile_load(const float2* tile, const float2* ptw, int r,
+                                              int j, bool valid, float2 (&v)[RowsT<LOG_M>::R]) {
   using P = RowsT<LOG_M>;
   constexpr int T = P::T, R = P::R, L = P::L, CP = S16 ? P::CPITCH16 : P::CPITCH;
   const int rr = valid ? r : 0;
@@ -422,7 +457,34 @@ __device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* lin
     const float2 wd = cmulc(D, split_tw<LOG_M, T>(ptw, ptw + L, j, u));   // D * exp(+2 pi i k / M)
     v[u] = valid ? make_float2(S.x - wd.y, S.y + wd.x) : make_float2(0.f, 0.f);
   }
-  line_fft_any<L, R, +1>(v, line, j, 1 + r, twl, ptw + L);
+}
+
+template <int LOG_M, bool S16 = false>
+__device__ __forceinline__ void c2r_tile_compute(const float2* tile, float2* line,
+                                                 const float2* twl, const float2* ptw, int r,
+                                                 int j, bool valid,
+                                                 float2 (&v)[RowsT<LOG_M>::R]) {
+  using P = RowsT<LOG_M>;
+  c2r_tile_load<LOG_M, S16>(tile, ptw, r, j, valid, v);
+  line_fft_any<P::L, P::R, +1>(v, line, j, 1 + r, twl, ptw + P::L);
+}
+
+// Row r of the inverse FFT's output v to out + base (float32 or bfloat16).
+template <int LOG_M, bool BF16OUT>
+__device__ __forceinline__ void c2r_store_row(const float2 (&v)[RowsT<LOG_M>::R], void* out,
+                                              size_t base, int j) {
+  using P = RowsT<LOG_M>;
+#pragma unroll
+  for (int u = 0; u < P::R; ++u) {
+    const int p = j + u * P::T;
+    if constexpr (BF16OUT) {
+      __nv_bfloat162 h = __floats2bfloat162_rn(v[u].x, v[u].y);
+      __stcs(reinterpret_cast<unsigned int*>(static_cast<__nv_bfloat16*>(out) + base + 2 * p),
+             *reinterpret_cast<unsigned int*>(&h));
+    } else {
+      __stcs(reinterpret_cast<float2*>(static_cast<float*>(out) + base + 2 * p), v[u]);
+    }
+  }
 }
 
 // C2R of one staged tile and the store of row r to out + base.
@@ -450,10 +512,26 @@ __device__ __forceinline__ void c2r_tile_body(const float2* tile, float2* line,
 }
 
 // S16: the staged half spectra are bfloat16 (the bfloat16 decomposition).
-template <int LOG_M, bool BF16OUT, bool S16>
-__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_rows_c2r_t(RowsTC2RArgs a) {
+// Three CTAs per SM where one staged tile, the work buffers and the
+// twiddles fit a third of the SM's shared memory: one stage, refilled once
+// the tile's split has read it (c2r_t sizes the launch accordingly).
+template <int LOG_M, bool S16>
+__host__ __device__ constexpr bool c2r_occ3() {
   using P = RowsT<LOG_M>;
-  constexpr int T = P::T, R = P::R, L = P::L, TR = P::TR, NST = S16 ? P::CNST16 : P::CNST;
+  return 3 * ((S16 ? P::CSTAGE16 : P::CSTAGE) + P::WORK + P::TWB + 1024) <= 228 * 1024;
+}
+template <int LOG_M, bool S16>
+__host__ __device__ constexpr int c2r_nst() {
+  using P = RowsT<LOG_M>;
+  return c2r_occ3<LOG_M, S16>() ? 1 : (S16 ? P::CNST16 : P::CNST);
+}
+
+template <int LOG_M, bool BF16OUT, bool S16>
+__global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, (c2r_occ3<LOG_M, S16>() ? 3 : RowsT<LOG_M>::MINB))
+    k_rows_c2r_t(RowsTC2RArgs a) {
+  using P = RowsT<LOG_M>;
+  constexpr int T = P::T, R = P::R, L = P::L, TR = P::TR, NST = c2r_nst<LOG_M, S16>();
+  constexpr bool EARLY = c2r_occ3<LOG_M, S16>();
   constexpr size_t SW = (S16 ? P::CSTAGE16 : P::CSTAGE) / sizeof(float2);
   extern __shared__ __align__(16) float2 smem[];
   float2* stages = smem;
@@ -471,10 +549,24 @@ __global__ void __launch_bounds__(RowsT<LOG_M>::THREADS, RowsT<LOG_M>::MINB) k_r
   LineTw<L, R>::fill(twl, a.tw, tid, P::THREADS);
   for (int p = tid; p < L; p += P::THREADS) ptw[p] = twiddle<-1>(a.tw, p, LOG_M);
   LineTwB<L, R>::fill(ptw + L, a.tw, tid, P::THREADS);
-  if (NST == 2 && blockIdx.x < ntiles) c2r_issue<LOG_M, S16>(a, stages, blockIdx.x, tid);
+  if ((NST == 2 || EARLY) && blockIdx.x < ntiles) c2r_issue<LOG_M, S16>(a, stages, blockIdx.x, tid);
   cp_async_commit();
   int k = 0;
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x, ++k) {
+    if constexpr (EARLY) {
+      cp_async_wait0();
+      __syncthreads();
+      const int s = t / tiles_per_sub, y0 = (t % tiles_per_sub) * TR;
+      float2 v[R];
+      c2r_tile_load<LOG_M, S16>(stages, ptw, r, j, valid, v);
+      __syncthreads();                     // the stage is read: refill it with the next tile
+      if (t + (int)gridDim.x < ntiles) c2r_issue<LOG_M, S16>(a, stages, t + gridDim.x, tid);
+      cp_async_commit();
+      line_fft_any<L, R, +1>(v, line, j, 1 + r, twl, ptw + L);
+      if (valid && SHL_IN((size_t)s * a.N + y0 + rr, (size_t)a.nsub * a.N, CHK_C2R_OUT))
+        c2r_store_row<LOG_M, BF16OUT>(v, a.out, ((size_t)s * a.N + y0 + rr) * P::M, j);
+      continue;
+    }
     const int tn = NST == 2 ? t + gridDim.x : t;
     if (tn < ntiles) c2r_issue<LOG_M, S16>(a, stages + ((k + 1) % NST) * SW, tn, tid);
     cp_async_commit();
@@ -1027,11 +1119,11 @@ static cudaError_t r2c_t(InMode mode, bool th, const RowsTArgs& a, cudaStream_t 
   using P = RowsT<LOG_M>;
   const int ntiles = a.nsub * (a.N / P::TR);
   if (ntiles == 0) return cudaSuccess;
-  const int grid = std::min(ntiles, sm_count() * P::MINB);
   cudaError_t e;
 #define SHL_LAUNCH(INM, TH)                                                         \
   do {                                                                              \
     const size_t sm = r2c_nst<LOG_M, INM>() * r2c_stage_bytes<LOG_M, INM>() + P::WORK + P::TWB; \
+    const int grid = std::min(ntiles, sm_count() * r2c_minb<LOG_M, INM>());         \
     if ((e = prep(k_rows_r2c_t<LOG_M, INM, TH>, sm))) return e;                     \
     k_rows_r2c_t<LOG_M, INM, TH><<<grid, P::THREADS, sm, st>>>(a);                   \
   } while (0)
@@ -1047,14 +1139,14 @@ static cudaError_t c2r_t(bool bf16, bool s16, const RowsTC2RArgs& a, cudaStream_
   using P = RowsT<LOG_M>;
   const int ntiles = a.nsub * (a.N / P::TR);
   if (ntiles == 0) return cudaSuccess;
-  const int grid = std::min(ntiles, sm_count() * P::MINB);
-  const size_t sm = (s16 ? P::CNST16 * P::CSTAGE16 : P::CNST * P::CSTAGE) + P::WORK + P::TWB;
   cudaError_t e;
-#define SHL_C2R(B, S)                                                   \
-  if (bf16 == B && s16 == S) {                                          \
-    if ((e = prep(k_rows_c2r_t<LOG_M, B, S>, sm))) return e;            \
-    k_rows_c2r_t<LOG_M, B, S><<<grid, P::THREADS, sm, st>>>(a);         \
-    return cudaGetLastError();                                          \
+#define SHL_C2R(B, S)                                                                     \
+  if (bf16 == B && s16 == S) {                                                            \
+    const size_t sm = c2r_nst<LOG_M, S>() * (S ? P::CSTAGE16 : P::CSTAGE) + P::WORK + P::TWB; \
+    const int g = std::min(ntiles, sm_count() * (c2r_occ3<LOG_M, S>() ? 3 : P::MINB));    \
+    if ((e = prep(k_rows_c2r_t<LOG_M, B, S>, sm))) return e;                              \
+    k_rows_c2r_t<LOG_M, B, S><<<g, P::THREADS, sm, st>>>(a);                              \
+    return cudaGetLastError();                                                            \
   }
   SHL_C2R(true, true) SHL_C2R(true, false) SHL_C2R(false, false)
 #undef SHL_C2R
