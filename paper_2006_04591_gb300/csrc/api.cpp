@@ -467,12 +467,13 @@ shl_status decompose_impl(const shl_bank* b, shl::InMode mode, const float* x,
   // bfloat16 coefficients: the staged half spectra between the column and the
   // row pass are bfloat16 too (half the staging traffic; the rounding is of
   // the size of the coefficients' own)
-  const bool s16 = dtype == SHL_BF16 && !tc;
+  const bool s16 = dtype == SHL_BF16;
   for (int s0 = 0; s0 < total; s0 += S) {
     const int Sc = std::min(S, total - s0);
     if (tc) {
       Launch L_("dec_lines_tc", st);
-      e = shl::launch_dec_lines_tc(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch);
+      e = shl::launch_dec_lines_tc(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch,
+                                    s16);
     } else {
       Launch L_("dec_lines", st);
       e = shl::launch_dec_lines(N, X, Z, b->dG, invW, scale, Mh, K, s0, Sc, b->dTw, st, batch, s16);

@@ -43,11 +43,12 @@ cudaError_t launch_rec_lines(int N, const float2* stage, float2* acc, const floa
                              const float* invW, float scale, int Mh, int K, int s0, int Sc,
                              const float2* tw, cudaStream_t st, int nimg);
 // Column pass of the bfloat16-output decomposition on the tensor cores
-// (tc_dft.cu, N = 512 only): the same staging planes as launch_dec_lines.
+// (tc_dft.cu, N = 512 only): the same staging planes as launch_dec_lines
+// (s16: bfloat16 planes).
 bool dec_lines_tc_supported(int N, int Mh);
-cudaError_t launch_dec_lines_tc(int N, const float2* X, float2* out, const float* G,
+cudaError_t launch_dec_lines_tc(int N, const float2* X, void* out, const float* G,
                                 const float* invW, float scale, int Mh, int K, int s0, int S,
-                                const float2* tw, cudaStream_t st, int nimg);
+                                const float2* tw, cudaStream_t st, int nimg, bool s16 = false);
 // Error flag of its bounded MMA waits and its checked-build guard word,
 // read and cleared.
 cudaError_t read_dft_error(unsigned* flag);

@@ -6,8 +6,9 @@
 //   Z_l[y] = sum_ky V_l[ky] exp(+2 pi i ky y / 512),
 //   V_l[ky] = X_b[kx][ky] * G_i[kx][ky] * scale [* 1/W[kx][ky]]
 // (the filter product and inverse column transform of Sec. 3.4), written to
-// the float32 staging plane for the row pass.  The 512-point DFT is split as
-// ky = n1 + 16 n2, y = k2 + 32 k1 (Cooley-Tukey, 32 x 16):
+// the staging plane of the row pass (bfloat16 pairs, or float2).  The
+// 512-point DFT is split as ky = n1 + 16 n2, y = k2 + 32 k1 (Cooley-Tukey,
+// 32 x 16):
 //   stage 1  Y[k2][n1] = sum_n2 exp(2 pi i n2 k2 / 32) V[n1 + 16 n2]
 //   twiddle  T[k2][n1] = exp(2 pi i n1 k2 / 512) Y[k2][n1]
 //   stage 2  Z[k2 + 32 k1] = sum_n1 exp(2 pi i n1 k1 / 16) T[k2][n1]
@@ -18,17 +19,19 @@
 //            (M = 128: rows 64..127 repeat rows 0..63, N = 8 lines x 16 n1 = 128, K = 64)
 //   stage 2  D2[(l, k2)][2 k1 + c] = sum_{(n1, c')} T[(l, k2)][2 n1 + c'] F16[2 k1 + c][2 n1 + c']
 //            (two M = 128 tiles of 4 lines x 32 k2, N = 32, K = 32)
-// One thread fetches the next tile's spectrum and filter lines (contiguous
-// 4 KB and 2 KB runs) with bulk copies (TMA) while the current tile runs its
-// stages; the CTA forms V from them.  Operands sit in shared memory in the
-// no-swizzle K-major core-matrix layout [K / 8][row][8 elements] (16 bytes
-// per row and 8-element group).  Between
-// the stages every thread reads one TMEM lane (a k2 and a re/im component)
-// of D1, takes the other component from its neighbour lane, applies the
-// twiddle and writes T as the stage-2 A operand; the stage-2 accumulators
-// reuse D1's columns.  The waits on the MMAs' mbarrier are bounded: when
-// one runs out the kernel records it (read by shl_sync), waits once more
-// for the MMAs and copies in flight, frees its TMEM and returns.
+// Operands sit in shared memory in the no-swizzle K-major core-matrix
+// layout [K / 8][row][8 elements] (16 bytes per row and 8-element group).
+// The work of a tile is split over warp roles that run concurrently on
+// different tiles: one warp copies a tile's spectrum and filter lines
+// (contiguous 4 KB and 2 KB runs) with bulk copies (TMA); four warps form
+// V from them; one thread issues both stages' MMAs; four warps read D1
+// (every thread one TMEM lane, a k2 and a re/im component, the other
+// component from its neighbour lane), apply the twiddle and write T; four
+// warps read D2 and store the lines.  Line slots, V, D1, T and D2 are
+// two-slot rings handed between the roles by mbarriers (MMA completion
+// through tcgen05.commit).  Every wait is bounded: when one runs out the
+// kernel records it (read by shl_sync), the other roles stop at their next
+// wait, the copies and MMAs in flight are waited for, and TMEM is freed.
 //
 // bfloat16 operands (8-bit mantissa) bound the relative error of Z near
 // 2^-8; this pass serves only the decomposition whose coefficients are
@@ -50,35 +53,50 @@ __device__ unsigned int g_dft_err = 0;
 
 constexpr int TD_N = 512;
 constexpr int TD_LINES = 8;                    // lines per tile
-constexpr int TD_THREADS = 256;
+// Roles by warp: 0-3 read out stage 1 (TMEM lane quarters 0-3), 4-7 read out
+// stage 2 and store, 8-11 form the stage-1 operand, 12 copies lines, 13
+// issues the MMAs.  Each hand-over is a two-slot ring of mbarrier pairs.
+constexpr int W_RD1 = 0, W_RD2 = 4, W_CONV = 8, W_COPY = 12, W_MMA = 13;
+constexpr int TD_THREADS = 14 * 32;
+constexpr int GROUP = 128;                     // threads of one 4-warp role
 constexpr unsigned TD_SPIN_LIMIT = 1u << 22;
-constexpr uint32_t TD_COLS = 128;              // TMEM columns (D1; D2 reuses 0..63)
+// TMEM: D1 of even / odd tiles at columns 0 / 128, D2 at 256 / 320
+constexpr uint32_t TD_COLS = 512;
+constexpr uint32_t D1_COL = 0, D2_COL = 256;
 
-// shared-memory layout (bytes); LBO = stride between K groups
+// shared-memory layout (bytes); LBO = stride between K groups.  The line
+// slots, V (B1) and T (A2) are two-slot rings: tile k uses slot k & 1.
 constexpr uint32_t A1_LBO = 128 * 16;          // F32 real form, 128 rows x 64 K
 constexpr uint32_t A1_BYTES = 8 * A1_LBO;
 constexpr uint32_t B1_LBO = 128 * 16;          // V, 128 rows (l, n1) x 64 K
 constexpr uint32_t B1_BYTES = 8 * B1_LBO;
-constexpr uint32_t A2_LBO = 128 * 16 + 32;     // T, 128 rows x 32 K per tile; +32 spreads banks
+constexpr uint32_t A2_LBO = 128 * 16 + 32;     // T, 128 rows x 32 K per M tile; +32 spreads banks
 constexpr uint32_t A2_TILE = 4 * A2_LBO;
 constexpr uint32_t A2_BYTES = 2 * A2_TILE;
 constexpr uint32_t B2_LBO = 32 * 16;           // F16 real form, 32 rows x 32 K
 constexpr uint32_t B2_BYTES = 4 * B2_LBO;
-constexpr uint32_t RX_BYTES = TD_LINES * TD_N * 8;   // the tile's spectrum lines, float2
+constexpr uint32_t RX_BYTES = TD_LINES * TD_N * 8;   // a tile's spectrum lines, float2
 constexpr uint32_t RG_BYTES = TD_LINES * TD_N * 4;   // its filter lines, float
-constexpr uint32_t OFF_A1 = 0, OFF_B1 = OFF_A1 + A1_BYTES, OFF_A2 = OFF_B1 + B1_BYTES,
-                   OFF_B2 = OFF_A2 + A2_BYTES, OFF_TW = OFF_B2 + B2_BYTES,
-                   OFF_RX = OFF_TW + 32 * 16 * 8, OFF_RG = OFF_RX + RX_BYTES;
-constexpr uint32_t TD_SMEM = OFF_RG + RG_BYTES;
+constexpr uint32_t RAW_BYTES = RX_BYTES + RG_BYTES;
+constexpr uint32_t OFF_A1 = 0, OFF_B2 = OFF_A1 + A1_BYTES, OFF_TW = OFF_B2 + B2_BYTES,
+                   OFF_B1 = OFF_TW + 32 * 16 * 8, OFF_A2 = OFF_B1 + 2 * B1_BYTES,
+                   OFF_RAW = OFF_A2 + 2 * A2_BYTES;
+constexpr uint32_t TD_SMEM = OFF_RAW + 2 * RAW_BYTES;
+static_assert(TD_SMEM <= 227 * 1024, "tensor-core column pass does not fit shared memory");
+
+// mbarriers, two slots each: FULL / EMPTY of the line slots, V, D1, T, D2
+enum : int { RAW_FULL = 0, RAW_EMPTY = 2, B1_FULL = 4, B1_EMPTY = 6, D1_FULL = 8, D1_EMPTY = 10,
+             A2_FULL = 12, A2_EMPTY = 14, D2_FULL = 16, D2_EMPTY = 18, NBAR = 20 };
 
 struct DftArgs {
   const float2* X;       // image spectra [nimg][Mh][512]
-  float2* out;           // staging [S][Mh][512]
+  void* out;             // staging [S][Mh][512], float2 or (s16) bfloat162
   const float* G;        // [K][Mh][512]
   const float* invW;     // [Mh][512] or null
   const float2* tw;      // exp(-2 pi i q / TW_P)
   float scale;
   int Mh, K, s0, nlines, nimg;
+  int s16;               // bfloat16 staging
 };
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
@@ -196,19 +214,56 @@ __device__ __forceinline__ void fetch_tile(const DftArgs& a, int tile, uint32_t 
       : "r"(ADDR)                                                                           \
       : "memory")
 
-__global__ void __launch_bounds__(TD_THREADS, 2) k_dec_lines_tc(DftArgs a) {
+// Wait for phase `parity` of mbarrier `bar`.  false when the wait runs out
+// (the role records it in *fail) or another role has failed: the caller's
+// role then stops.
+__device__ __forceinline__ bool role_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
+  for (unsigned i = 0; i < TD_SPIN_LIMIT; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(done) : "r"(bar), "r"(parity) : "memory");
+    if (done) return true;
+    if ((i & 255u) == 255u && *fail) return false;
+  }
+  *fail = 1;
+  return false;
+}
+
+// role_wait taken by a whole warp: every lane goes on or every lane stops.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int* fail) {
+  return __all_sync(0xffffffffu, role_wait(bar, parity, fail));
+}
+
+__device__ __forceinline__ void arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// One CTA per SM walks the tiles blockIdx.x + k gridDim.x, k = 0 .. nk-1,
+// each role at its own pace:
+//   copy warp     lines of tile k -> line slot k & 1          (after the slot is empty)
+//   conversion    V = X G scale [/W] of tile k -> B1 slot      (after its lines arrived)
+//   MMA thread    stage 1 of tile k -> D1 slot, then stage 2 of tile k-1 -> D2 slot
+//   read-out 1    D1 of tile k, twiddled -> T (A2 slot)
+//   read-out 2    D2 of tile k -> staging rows
+// Every slot is handed on by a FULL mbarrier and back by an EMPTY one (MMA
+// completion arrives through tcgen05.commit), so up to two tiles are in
+// each stage at once and the stages overlap across tiles.
+__global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
   extern __shared__ __align__(128) uint8_t sm[];
-  __shared__ __align__(8) uint64_t mbar[2];        // [0] MMAs, [1] line copies
+  __shared__ __align__(8) uint64_t mb[NBAR];
   __shared__ uint32_t tmem_slot;
+  __shared__ int s_fail, s_copies, s_mma1, s_mma2;   // failure flag; tiles issued per async unit
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint8_t* A1 = sm + OFF_A1;
-  uint8_t* B1 = sm + OFF_B1;
-  uint8_t* A2 = sm + OFF_A2;
   uint8_t* B2 = sm + OFF_B2;
   float2* TW = reinterpret_cast<float2*>(sm + OFF_TW);
-  const float2* RX = reinterpret_cast<const float2*>(sm + OFF_RX);
-  const float* RG = reinterpret_cast<const float*>(sm + OFF_RG);
   const int ntiles = (a.nlines + TD_LINES - 1) / TD_LINES;
+  const int nk = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto tile_of = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
+  auto bar = [&](int i) { return su32(&mb[i]); };
+  volatile int* fail = &s_fail;
 
   // constant operands: F32 (rows 2 k2 + c, repeated for rows 64..127), F16,
   // and the twiddles exp(2 pi i n1 k2 / 512)
@@ -241,149 +296,217 @@ __global__ void __launch_bounds__(TD_THREADS, 2) k_dec_lines_tc(DftArgs a) {
                      su32(&tmem_slot)), "r"(TD_COLS) : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  const uint32_t bar = su32(&mbar[0]), rbar = su32(&mbar[1]);
-  const uint32_t rx = su32(sm + OFF_RX), rg = su32(sm + OFF_RG);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(rbar) : "memory");
+    for (int i = 0; i < NBAR; ++i) {
+      const int kind = i & ~1;
+      const unsigned count = (kind == RAW_EMPTY || kind == B1_FULL || kind == D1_EMPTY ||
+                              kind == A2_FULL || kind == D2_EMPTY) ? GROUP : 1;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(count) : "memory");
+    }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
+    s_copies = s_mma1 = s_mma2 = 0;
   }
-  __syncwarp();
-  if (warp == 0 && (int)blockIdx.x < ntiles) fetch_tile(a, blockIdx.x, rx, rg, rbar, lane);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // constant operands
   fence_before();
   __syncthreads();
   fence_after();
   const uint32_t tmem = tmem_slot;
-  const uint32_t a1 = su32(A1), b1 = su32(B1), a2 = su32(A2), b2 = su32(B2);
 
-  // this thread's D1 lane: quarter q, k2 = 16 (q & 1) + lane / 2, component c
-  const int q = warp & 3, c = lane & 1, k2 = 16 * (q & 1) + (lane >> 1);
-  const int lpair = (q >> 1) + 2 * (warp >> 2);    // D1 lines 2 lpair, 2 lpair + 1
-  float2 tw8[8];
+  if (warp >= W_RD1 && warp < W_RD1 + 4) {
+    // stage-1 read-out: thread (quarter q, lane) holds row 32 q + lane of D1,
+    // i.e. k2 = 16 (q & 1) + lane / 2 and component c = lane & 1 (rows 64..127
+    // repeat 0..63: quarters 0, 1 take lines 0-3, quarters 2, 3 lines 4-7)
+    const int q = warp & 3, c = lane & 1, k2 = 16 * (q & 1) + (lane >> 1);
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    float2 tw8[8];
 #pragma unroll
-  for (int u = 0; u < 8; ++u) tw8[u] = TW[k2 * 16 + u + 8 * c];
-  // conversion items (l, n1, g): this thread's share n1, g fixed, l = lc, lc + 2, ...
-  const int n1 = tid & 15, g = (tid >> 4) & 7, lc = tid >> 7;
-
-  uint32_t phase = 0, rphase = 0;
-  int inflight = (int)blockIdx.x < ntiles ? 1 : 0;   // line copies issued and not waited on
-  bool failed = false, mma_pending = false;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int l0 = tile * TD_LINES;
-    bool ok = wait_bounded(rbar, rphase);
-    if (__syncthreads_or(!ok)) { failed = true; break; }
-    rphase ^= 1u;
-    inflight = 0;
-    // V = X * G * scale [* 1/W] -> bfloat16 B1 rows (l, n1), K group g = n2 4 g .. 4 g + 3
-    const int sl0 = l0 / a.Mh, kx0 = l0 - sl0 * a.Mh;
-#pragma unroll
-    for (int k = 0; k < TD_LINES / 2; ++k) {
-      const int l = lc + 2 * k;
-      uint32_t w[4] = {0u, 0u, 0u, 0u};
-      if (l0 + l < a.nlines) {
-        const float* Wp = nullptr;
-        if (a.invW) {
-          const int kx = kx0 + l >= a.Mh ? kx0 + l - a.Mh : kx0 + l;
-          Wp = a.invW + (size_t)kx * TD_N;
-        }
-#pragma unroll
-        for (int t = 0; t < 4; ++t) {
-          const int ky = n1 + 16 * (4 * g + t);
-          const float2 x = RX[l * TD_N + ky];
-          float gv = RG[l * TD_N + ky] * a.scale;
-          if (Wp) gv *= __ldg(Wp + ky);
-          w[t] = pk(x.x * gv, x.y * gv);
-        }
-      }
-      *reinterpret_cast<uint4*>(B1 + g * B1_LBO + (l * 16 + n1) * 16) =
-          make_uint4(w[0], w[1], w[2], w[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before();
-    __syncthreads();                                 // B1 written, RX / RG read
-    if (warp == 0) {
-      if (lane == 0) {
-        fence_after();
-#pragma unroll
-        for (int s = 0; s < 4; ++s)                  // stage 1: 4 K steps of 16
-          mma(tmem, mdesc(a1 + 2 * s * A1_LBO, A1_LBO, 128),
-              mdesc(b1 + 2 * s * B1_LBO, B1_LBO, 128), idesc(128, 128), s > 0);
-        commit(bar);
-      }
-      __syncwarp();
-      const int next = tile + gridDim.x;             // lands during this tile's stages
-      if (next < ntiles) fetch_tile(a, next, rx, rg, rbar, lane);
-    }
-    inflight = tile + (int)gridDim.x < ntiles ? 1 : 0;
-    ok = wait_bounded(bar, phase);
-    if (__syncthreads_or(!ok)) { failed = mma_pending = true; break; }
-    phase ^= 1u;
-    fence_after();
-
-    // D1 -> twiddled T -> A2 (lane pairs swap components: c = 0 forms n1 0..7, c = 1 n1 8..15)
-    uint32_t d1[2][16];
-    TD_LD16(d1[0], tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * lpair));
-    TD_LD16(d1[1], tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * lpair + 16));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int l = 2 * lpair + h;
-      const uint32_t* v = d1[h];
-      float re[8], im[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const float send = __uint_as_float(c ? v[u] : v[u + 8]);
-        const float got = __shfl_xor_sync(0xffffffffu, send, 1);
-        const float mine = __uint_as_float(c ? v[u + 8] : v[u]);
-        const float yr = c ? got : mine, yi = c ? mine : got;
-        re[u] = yr * tw8[u].x - yi * tw8[u].y;
-        im[u] = yr * tw8[u].y + yi * tw8[u].x;
-      }
-      const int mt = l >> 2, r2 = (l & 3) * 32 + k2;
-      uint8_t* dst = A2 + mt * A2_TILE + (2 * c) * A2_LBO + r2 * 16;
-      *reinterpret_cast<uint4*>(dst) =
-          make_uint4(pk(re[0], im[0]), pk(re[1], im[1]), pk(re[2], im[2]), pk(re[3], im[3]));
-      *reinterpret_cast<uint4*>(dst + A2_LBO) =
-          make_uint4(pk(re[4], im[4]), pk(re[5], im[5]), pk(re[6], im[6]), pk(re[7], im[7]));
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    fence_before();
-    __syncthreads();
-    if (tid == 0) {                                  // stage 2: 2 M tiles x 2 K steps
+    for (int u = 0; u < 8; ++u) tw8[u] = TW[k2 * 16 + u + 8 * c];
+    for (int k = 0; k < nk; ++k) {
+      const int s = k & 1;
+      const uint32_t ph = (k >> 1) & 1;
+      if (!warp_wait(bar(D1_FULL + s), ph, fail) || !warp_wait(bar(A2_EMPTY + s), ph ^ 1, fail))
+        break;
       fence_after();
+      uint8_t* A2 = sm + OFF_A2 + s * A2_BYTES;
 #pragma unroll
-      for (int mt = 0; mt < 2; ++mt)
+      for (int i = 0; i < 2; ++i) {
+        const int lpair = 2 * (q >> 1) + i;          // lines 2 lpair, 2 lpair + 1
+        uint32_t d1v[2][16];
+        const uint32_t d1 = tmem + lanes + D1_COL + (uint32_t)(128 * s + 32 * lpair);
+        TD_LD16(d1v[0], d1);
+        TD_LD16(d1v[1], d1 + 16u);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (i == 1) {                                // this thread's reads of D1 are done
+          fence_before();
+          arrive(bar(D1_EMPTY + s));
+        }
 #pragma unroll
-        for (int s = 0; s < 2; ++s)
-          mma(tmem + (uint32_t)(32 * mt), mdesc(a2 + mt * A2_TILE + 2 * s * A2_LBO, A2_LBO, 128),
-              mdesc(b2 + 2 * s * B2_LBO, B2_LBO, 128), idesc(128, 32), s > 0);
-      commit(bar);
+        for (int h = 0; h < 2; ++h) {
+          const int l = 2 * lpair + h;
+          const uint32_t* v = d1v[h];
+          float re[8], im[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const float send = __uint_as_float(c ? v[u] : v[u + 8]);
+            const float got = __shfl_xor_sync(0xffffffffu, send, 1);
+            const float mine = __uint_as_float(c ? v[u + 8] : v[u]);
+            const float yr = c ? got : mine, yi = c ? mine : got;
+            re[u] = yr * tw8[u].x - yi * tw8[u].y;
+            im[u] = yr * tw8[u].y + yi * tw8[u].x;
+          }
+          const int mt = l >> 2, r2 = (l & 3) * 32 + k2;
+          uint8_t* dst = A2 + mt * A2_TILE + (2 * c) * A2_LBO + r2 * 16;
+          *reinterpret_cast<uint4*>(dst) =
+              make_uint4(pk(re[0], im[0]), pk(re[1], im[1]), pk(re[2], im[2]), pk(re[3], im[3]));
+          *reinterpret_cast<uint4*>(dst + A2_LBO) =
+              make_uint4(pk(re[4], im[4]), pk(re[5], im[5]), pk(re[6], im[6]), pk(re[7], im[7]));
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      arrive(bar(A2_FULL + s));
     }
-    ok = wait_bounded(bar, phase);
-    if (__syncthreads_or(!ok)) { failed = mma_pending = true; break; }
-    phase ^= 1u;
-    fence_after();
-
-    // D2 -> staging: warp w reads line 4 (w / 4) + q, lane k2: Z[k2 + 32 k1], k1 = 0..15
-    {
-      const int mt = warp >> 2, line = l0 + 4 * mt + q;
-      uint32_t v[32];
-      TD_LD16(v, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * mt));
-      TD_LD16(v + 16, tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * mt + 16));
+  } else if (warp >= W_RD2 && warp < W_RD2 + 4) {
+    // stage-2 read-out: quarter q holds rows (l & 3) 32 + k2 of both M tiles,
+    // i.e. lines 4 mt + q, k2 = lane; columns 2 k1 + c
+    const int q = warp & 3;
+    const uint32_t lanes = (uint32_t)(32 * q) << 16;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k & 1;
+      if (!warp_wait(bar(D2_FULL + s), (k >> 1) & 1, fail)) break;
+      fence_after();
+      uint32_t v[2][32];
+      const uint32_t d2 = tmem + lanes + D2_COL + (uint32_t)(64 * s);
+      TD_LD16(v[0], d2);
+      TD_LD16(v[0] + 16, d2 + 16u);
+      TD_LD16(v[1], d2 + 32u);
+      TD_LD16(v[1] + 16, d2 + 48u);
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      if (line < a.nlines && SHL_IN(line, a.nlines, CHK_TC_OUT)) {
-        float2* o = a.out + (size_t)line * TD_N + lane;
+      fence_before();
+      arrive(bar(D2_EMPTY + s));
 #pragma unroll
-        for (int k1 = 0; k1 < 16; ++k1)
-          o[32 * k1] = make_float2(__uint_as_float(v[2 * k1]), __uint_as_float(v[2 * k1 + 1]));
+      for (int mt = 0; mt < 2; ++mt) {
+        const int line = tile_of(k) * TD_LINES + 4 * mt + q;
+        if (line < a.nlines && SHL_IN(line, a.nlines, CHK_TC_OUT)) {
+          if (a.s16) {
+            __nv_bfloat162* o = static_cast<__nv_bfloat162*>(a.out) + (size_t)line * TD_N + lane;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1)
+              o[32 * k1] = __floats2bfloat162_rn(__uint_as_float(v[mt][2 * k1]),
+                                                 __uint_as_float(v[mt][2 * k1 + 1]));
+          } else {
+            float2* o = static_cast<float2*>(a.out) + (size_t)line * TD_N + lane;
+#pragma unroll
+            for (int k1 = 0; k1 < 16; ++k1)
+              o[32 * k1] = make_float2(__uint_as_float(v[mt][2 * k1]), __uint_as_float(v[mt][2 * k1 + 1]));
+          }
+        }
       }
     }
-    fence_before();                                  // TMEM reads done before the next MMAs
+  } else if (warp >= W_CONV && warp < W_CONV + 4) {
+    // V[(l, n1)][(n2, c)] of the tile's 8 lines: thread (n1, g) forms
+    // n2 = 4 g .. 4 g + 3 of every line (16-byte core-matrix rows)
+    const int ct = tid - W_CONV * 32;
+    const int n1 = ct & 15, g = (ct >> 4) & 7;
+    for (int k = 0; k < nk; ++k) {
+      const int s = k & 1;
+      const uint32_t ph = (k >> 1) & 1;
+      if (!warp_wait(bar(RAW_FULL + s), ph, fail) || !warp_wait(bar(B1_EMPTY + s), ph ^ 1, fail))
+        break;
+      const float2* RX = reinterpret_cast<const float2*>(sm + OFF_RAW + s * RAW_BYTES);
+      const float* RG = reinterpret_cast<const float*>(sm + OFF_RAW + s * RAW_BYTES + RX_BYTES);
+      uint8_t* B1 = sm + OFF_B1 + s * B1_BYTES;
+      const int l0 = tile_of(k) * TD_LINES;
+      const int sl0 = l0 / a.Mh, kx0 = l0 - sl0 * a.Mh;
+      uint4 pkd[TD_LINES];
+#pragma unroll
+      for (int l = 0; l < TD_LINES; ++l) {
+        uint32_t w[4] = {0u, 0u, 0u, 0u};
+        if (l0 + l < a.nlines) {
+          const float* Wp = nullptr;
+          if (a.invW) {
+            const int kx = kx0 + l >= a.Mh ? kx0 + l - a.Mh : kx0 + l;
+            Wp = a.invW + (size_t)kx * TD_N;
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int ky = n1 + 16 * (4 * g + t);
+            const float2 x = RX[l * TD_N + ky];
+            float gv = RG[l * TD_N + ky] * a.scale;
+            if (Wp) gv *= __ldg(Wp + ky);
+            w[t] = pk(x.x * gv, x.y * gv);
+          }
+        }
+        pkd[l] = make_uint4(w[0], w[1], w[2], w[3]);
+      }
+      arrive(bar(RAW_EMPTY + s));                    // the line slot is read
+#pragma unroll
+      for (int l = 0; l < TD_LINES; ++l)
+        *reinterpret_cast<uint4*>(B1 + g * B1_LBO + (l * 16 + n1) * 16) = pkd[l];
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      arrive(bar(B1_FULL + s));
+    }
+  } else if (warp == W_COPY) {
+    for (int k = 0; k < nk; ++k) {
+      const int s = k & 1;
+      if (!warp_wait(bar(RAW_EMPTY + s), ((k >> 1) & 1) ^ 1, fail)) break;
+      fetch_tile(a, tile_of(k), su32(sm + OFF_RAW + s * RAW_BYTES),
+                 su32(sm + OFF_RAW + s * RAW_BYTES + RX_BYTES), bar(RAW_FULL + s), lane);
+      if (lane == 0) s_copies = k + 1;
+    }
+  } else if (warp == W_MMA && lane == 0) {
+    const uint32_t a1 = su32(A1), b2 = su32(B2);
+    for (int k = 0; k <= nk; ++k) {
+      if (k < nk) {                                  // stage 1 of tile k
+        const int s = k & 1;
+        const uint32_t ph = (k >> 1) & 1;
+        if (!role_wait(bar(B1_FULL + s), ph, fail) || !role_wait(bar(D1_EMPTY + s), ph ^ 1, fail))
+          break;
+        fence_after();
+        const uint32_t b1 = su32(sm + OFF_B1 + s * B1_BYTES), d1 = tmem + D1_COL + (uint32_t)(128 * s);
+#pragma unroll
+        for (int st = 0; st < 4; ++st)
+          mma(d1, mdesc(a1 + 2 * st * A1_LBO, A1_LBO, 128), mdesc(b1 + 2 * st * B1_LBO, B1_LBO, 128),
+              idesc(128, 128), st > 0);
+        commit(bar(D1_FULL + s));
+        commit(bar(B1_EMPTY + s));
+        s_mma1 = k + 1;
+      }
+      if (k >= 1) {                                  // stage 2 of tile k - 1
+        const int j = k - 1, s = j & 1;
+        const uint32_t ph = (j >> 1) & 1;
+        if (!role_wait(bar(A2_FULL + s), ph, fail) || !role_wait(bar(D2_EMPTY + s), ph ^ 1, fail))
+          break;
+        fence_after();
+        const uint32_t a2 = su32(sm + OFF_A2 + s * A2_BYTES);
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int st = 0; st < 2; ++st)
+            mma(tmem + D2_COL + (uint32_t)(64 * s + 32 * mt),
+                mdesc(a2 + mt * A2_TILE + 2 * st * A2_LBO, A2_LBO, 128),
+                mdesc(b2 + 2 * st * B2_LBO, B2_LBO, 128), idesc(128, 32), st > 0);
+        commit(bar(D2_FULL + s));
+        commit(bar(A2_EMPTY + s));
+        s_mma2 = j + 1;
+      }
+    }
   }
-  if (failed && tid == 0) {
-    atomicOr(&g_dft_err, 1u);
-    if (mma_pending) wait_bounded(bar, phase);       // the MMAs whose wait ran out
-    if (inflight) wait_bounded(rbar, rphase);        // line copies still in flight
+
+  __syncthreads();
+  if (s_fail) {
+    // a wait ran out: let the copies and MMAs still in flight land (bounded)
+    // before TMEM is freed and the CTA's shared memory released
+    if (tid == 0) {
+      atomicOr(&g_dft_err, 1u);
+      for (int s = 0; s < 2; ++s) {
+        const int kc = s_copies - 1 - ((s_copies - 1 - s) & 1);   // last copied tile in slot s
+        if (kc >= 0) wait_bounded(bar(RAW_FULL + s), (kc >> 1) & 1);
+      }
+      if (s_mma1 > 0) wait_bounded(bar(D1_FULL + ((s_mma1 - 1) & 1)), ((s_mma1 - 1) >> 1) & 1);
+      if (s_mma2 > 0) wait_bounded(bar(D2_FULL + ((s_mma2 - 1) & 1)), ((s_mma2 - 1) >> 1) & 1);
+    }
+    __syncthreads();
   }
   fence_before();
   __syncthreads();
@@ -398,9 +521,9 @@ __global__ void __launch_bounds__(TD_THREADS, 2) k_dec_lines_tc(DftArgs a) {
 // A tile's 8 lines span at most two subbands when Mh >= 8.
 bool dec_lines_tc_supported(int N, int Mh) { return N == TD_N && Mh >= TD_LINES; }
 
-cudaError_t launch_dec_lines_tc(int N, const float2* X, float2* out, const float* G,
+cudaError_t launch_dec_lines_tc(int N, const float2* X, void* out, const float* G,
                                 const float* invW, float scale, int Mh, int K, int s0, int S,
-                                const float2* tw, cudaStream_t st, int nimg) {
+                                const float2* tw, cudaStream_t st, int nimg, bool s16) {
   if (S == 0) return cudaSuccess;
   if (!dec_lines_tc_supported(N, Mh) || S < 0) return cudaErrorInvalidValue;
   static int nsm[64] = {0};
@@ -414,9 +537,9 @@ cudaError_t launch_dec_lines_tc(int N, const float2* X, float2* out, const float
                                   (int)TD_SMEM)))
       return e;
   }
-  DftArgs a{X, out, G, invW, tw, scale, Mh, K, s0, S * Mh, nimg};
+  DftArgs a{X, out, G, invW, tw, scale, Mh, K, s0, S * Mh, nimg, s16 ? 1 : 0};
   const int ntiles = (a.nlines + TD_LINES - 1) / TD_LINES;
-  const int grid = ntiles < 2 * nsm[dev] ? ntiles : 2 * nsm[dev];   // two CTAs per SM
+  const int grid = ntiles < nsm[dev] ? ntiles : nsm[dev];   // one CTA per SM
   k_dec_lines_tc<<<grid, TD_THREADS, TD_SMEM, st>>>(a);
   return cudaGetLastError();
 }
