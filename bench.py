@@ -33,6 +33,7 @@ N_IMG, K_FILT, B_IMG, SCALES = 512, 49, 16, 4
 METRIC = "Shearlet coeffs/s fwd+inv at 512^2, 49 filters"
 UNIT = "coeffs/s"
 L2_FLUSH_BYTES = 512 << 20
+SWEEP_STEPS = 20                 # timed steps per point of the 1024 x 1024 sweep
 
 
 def _config(extra=None):
@@ -486,9 +487,6 @@ def run_gpu(args):
     clock_info = clocks.stop()
     clock_info["window"] = "timed, per-kernel-event and end-to-end passes"
 
-    coeffs_per_step = B * K * N * N * world
-    value = job_value(B * K * N * N, world, t_step)
-    dec_b, rec_b = _algorithmic_bytes(B, K, N, N)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -496,6 +494,43 @@ def run_gpu(args):
         pass
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # the 1024 x 1024 workload (K = 49) at batches 1..8, float32 and bfloat16
+    # coefficients: decompose + reconstruct per step, CUDA events, the L2
+    # flushed between steps
+    sweep = []
+    if world == 1 and not args.no_sweep:
+        n5 = 1024
+        b5 = S.Bank.create(n5, n5, SCALES, device=local)
+        x5 = torch.from_numpy(np.stack([synth.cartoon(n5, n5, 5000 + i) for i in range(8)])
+                              .astype(np.float32)).to(dev)
+        for b_ in (1, 2, 4, 8):
+            xs, xo = x5[:b_], torch.empty((b_, n5, n5), dtype=torch.float32, device=dev)
+            wd = b5.workspace(S.SHL_OP_DECOMPOSE, b_)
+            wr = b5.workspace(S.SHL_OP_RECONSTRUCT, b_)
+            for dt, s_ in ((torch.float32, 4), (torch.bfloat16, 2)):
+                cs = torch.empty((b_, b5.K, n5, n5), dtype=dt, device=dev)
+
+                def step5():
+                    b5.decompose(xs, out=cs, ws=wd)
+                    b5.reconstruct(cs, out=xo, ws=wr)
+
+                for _ in range(3):
+                    step5()
+                torch.cuda.synchronize()
+                err5 = ((xo - xs).abs().max() / xs.abs().max()).item()
+                t5 = sum(timed(step5, SWEEP_STEPS)) / SWEEP_STEPS / 1e3
+                d5, r5 = _algorithmic_bytes(b_, b5.K, n5, n5, s=s_)
+                sweep.append({"batch": b_, "coeff_dtype": "f32" if s_ == 4 else "bf16 (RNE)",
+                              "ms_per_step": t5 * 1e3, "value": b_ * b5.K * n5 * n5 / t5,
+                              "unit": UNIT, "frac_of_peak": (d5 + r5) / t5 / 1e9 / hbm_peak,
+                              "pr_rel_err": err5})
+                del cs
+        del x5, b5
+
+    coeffs_per_step = B * K * N * N * world
+    value = job_value(B * K * N * N, world, t_step)
+    dec_b, rec_b = _algorithmic_bytes(B, K, N, N)
 
     # dominant kernel and its algorithmic bytes per launch
     roof = roofline(prof, args.steps, B, K, N, N, 4, hbm_peak, peak_src)
@@ -540,6 +575,7 @@ def run_gpu(args):
             (t_pm, "two streams, one half batch each, the kernels reading and writing the "
                    "pinned host images, the halves overlapping", pm_err)]),
         "bf16": bf16_block,
+        "sweep_1024": sweep or None,
         "gpu_launches": launches,
         "clocks": clock_info,
         "pr_rel_err": err,
@@ -566,6 +602,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true",
+                    help="skip the 1024 x 1024 batch sweep (sweep_1024)")
     ap.add_argument("--cpu-table", action="store_true",
                     help="time the FP64 oracle at several workloads on the host cores and exit")
     args = ap.parse_args()
