@@ -162,6 +162,14 @@ struct Dft {
   }
 };
 
+// 8-byte asynchronous global -> shared copies (cp.async) and their waits.
+__device__ __forceinline__ void gcp_async8(void* smem_dst, const void* gmem_src) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void gcp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void gcp_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // One Stockham stage of radix R, one butterfly j = g Ns + k per thread:
 // twiddle input m by w^(m k P/(Ns R)), DFT_R, store output q at
 // g Ns R + q Ns + k.
@@ -488,20 +496,32 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols(const ColArgs a) {
   } else if constexpr (KIND == COL_REC) {
     // group blockIdx.z of image blockIdx.y: its subbands' column DFTs times
     // conj(G_i), summed in order of i in registers, written over the
-    // columns of the group's first staging plane (which only this CTA reads)
+    // columns of the group's first staging plane (which only this CTA reads).
+    // Three tile buffers rotate: subband s is transformed in `in` (with `al`
+    // as the Stockham partner) while the staged columns of subband s + 1 are
+    // copied (cp.async) into `nx`.
     const RecRange r = rec_range(a, blockIdx.y, blockIdx.z);
     if (r.lo >= r.hi) return;
     float2 acc[COL_ACC];
 #pragma unroll
     for (int u = 0; u < COL_ACC; ++u) acc[u] = make_float2(0.f, 0.f);
-    for (int s = r.lo; s < r.hi; ++s) {
-      const int i = s - r.b * a.K;
-      const float2* Ts = a.T + (size_t)(s - a.s0) * plane;
-      for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
-        const int y = qdiv(idx, rC), c = idx - y * C;
-        buf[c * a.pitch + y] = Ts[(size_t)y * W + col0 + c];
+    float2* in = sm + 2 * (size_t)a.C * a.pitch;
+    float2* al = buf;
+    float2* nx = alt;
+    for (int s = r.lo - 1; s < r.hi; ++s) {
+      if (s >= r.lo) gcp_wait_all();        // this thread's copies of subband s
+      if (s + 1 < r.hi) {                   // nx was last read before the loop's closing barrier
+        const float2* Ts = a.T + (size_t)(s + 1 - a.s0) * plane;
+        float2* dst = s >= r.lo ? nx : in;
+        for (int idx = threadIdx.x; idx < NC; idx += blockDim.x) {
+          const int y = qdiv(idx, rC), c = idx - y * C;
+          gcp_async8(dst + c * a.pitch + y, Ts + (size_t)y * W + col0 + c);
+        }
+        gcp_commit();
       }
-      float2* res = line_dft(buf, alt, C, a.pitch, p);
+      if (s < r.lo) continue;
+      const int i = s - r.b * a.K;
+      float2* res = line_dft(in, al, C, a.pitch, p);   // begins with a barrier
 #pragma unroll
       for (int u = 0; u < COL_ACC; ++u) {
         const int idx = threadIdx.x + u * COL_THREADS;
@@ -514,6 +534,10 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols(const ColArgs a) {
         }
       }
       __syncthreads();
+      float2* const t = in;                 // rotate: next input, its partner, the next target
+      in = nx;
+      nx = al;
+      al = t;
     }
     float2* part = a.T + (size_t)(r.lo - a.s0) * plane;
 #pragma unroll
@@ -747,6 +771,7 @@ cudaError_t launch_cols_rec(const LinePlan& pn, float2* T, float2* A, const void
   a.W = W; a.K = K; a.s0 = s0; a.S = S; a.C = col_lines(pn, W); a.pitch = pn.P + 1;
   const int nimg = S > 0 ? (s0 + S - 1) / K - s0 / K + 1 : 0;
   const size_t smem = 2 * (size_t)a.C * a.pitch * sizeof(float2);
+  const size_t smem_rec = 3 * (size_t)a.C * a.pitch * sizeof(float2);   // + the prefetch buffer
   const unsigned cb = (unsigned)((W + a.C - 1) / a.C);
   // subband groups per image: about four waves of CTAs (smem-bound residency)
   // with at least ceil(K / 16) subbands a group, so that one image's K
@@ -754,12 +779,12 @@ cudaError_t launch_cols_rec(const LinePlan& pn, float2* T, float2* A, const void
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long per_sm = std::max<long long>(1, (228 * 1024) / (long long)(smem + 1024));
+  const long long per_sm = std::max<long long>(1, (228 * 1024) / (long long)(smem_rec + 1024));
   const long long want = 4LL * std::max(sms, 1) * per_sm;
   const long long base = std::max<long long>(1, (long long)cb * nimg);
   a.groups = (int)std::max<long long>(1, std::min<long long>({(want + base - 1) / base, 16,
                                                               std::min(S, K)}));
-  cudaError_t e = launch(k_cols<COL_REC>, dim3(cb, nimg, a.groups), COL_THREADS, smem, st, a);
+  cudaError_t e = launch(k_cols<COL_REC>, dim3(cb, nimg, a.groups), COL_THREADS, smem_rec, st, a);
   if (e) return e;
   return launch(k_cols<COL_FIN>, dim3(cb, nimg), COL_THREADS, smem, st, a);
 }
