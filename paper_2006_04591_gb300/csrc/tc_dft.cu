@@ -23,11 +23,12 @@
 // layout [K / 8][row][8 elements] (16 bytes per row and 8-element group).
 // The work of a tile is split over warp roles that run concurrently on
 // different tiles: one warp copies a tile's spectrum and filter lines
-// (contiguous 4 KB and 2 KB runs) with bulk copies (TMA); four warps form
-// V from them; one thread issues both stages' MMAs; four warps read D1
-// (every thread one TMEM lane, a k2 and a re/im component, the other
-// component from its neighbour lane), apply the twiddle and write T; four
-// warps read D2 and store the lines.  Line slots, V, D1, T and D2 are
+// (two contiguous runs, or 4 KB and 2 KB lines where the tile crosses a
+// subband) with bulk copies (TMA); eight warps form V from them; one
+// thread issues both stages' MMAs; four warps read D1 (every thread one TMEM
+// lane, a k2 and a re/im component, the other component from its neighbour
+// lane), apply the twiddle and write T; four warps read D2 and store the
+// lines.  Line slots, V, D1, T and D2 are
 // two-slot rings handed between the roles by mbarriers (MMA completion
 // through tcgen05.commit).  Every wait is bounded: when one runs out the
 // kernel records it (read by shl_sync), the other roles stop at their next
@@ -39,6 +40,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "check.cuh"
@@ -54,11 +56,12 @@ __device__ unsigned int g_dft_err = 0;
 constexpr int TD_N = 512;
 constexpr int TD_LINES = 8;                    // lines per tile
 // Roles by warp: 0-3 read out stage 1 (TMEM lane quarters 0-3), 4-7 read out
-// stage 2 and store, 8-11 form the stage-1 operand, 12 copies lines, 13
+// stage 2 and store, 8-15 form the stage-1 operand, 16 copies lines, 17
 // issues the MMAs.  Each hand-over is a two-slot ring of mbarrier pairs.
-constexpr int W_RD1 = 0, W_RD2 = 4, W_CONV = 8, W_COPY = 12, W_MMA = 13;
-constexpr int TD_THREADS = 14 * 32;
-constexpr int GROUP = 128;                     // threads of one 4-warp role
+constexpr int W_RD1 = 0, W_RD2 = 4, W_CONV = 8, W_COPY = 16, W_MMA = 17;
+constexpr int TD_THREADS = 18 * 32;
+constexpr int GROUP = 128;                     // threads of a read-out role
+constexpr int CGROUP = 256;                    // threads of the conversion role
 constexpr unsigned TD_SPIN_LIMIT = 1u << 22;
 // TMEM: D1 of even / odd tiles at columns 0 / 128, D2 at 256 / 320
 constexpr uint32_t TD_COLS = 512;
@@ -75,8 +78,8 @@ constexpr uint32_t A2_TILE = 4 * A2_LBO;
 constexpr uint32_t A2_BYTES = 2 * A2_TILE;
 constexpr uint32_t B2_LBO = 32 * 16;           // F16 real form, 32 rows x 32 K
 constexpr uint32_t B2_BYTES = 4 * B2_LBO;
-constexpr uint32_t RX_BYTES = TD_LINES * TD_N * 8;   // a tile's spectrum lines, float2
-constexpr uint32_t RG_BYTES = TD_LINES * TD_N * 4;   // its filter lines, float
+constexpr uint32_t RX_BYTES = 2 * TD_N * 8;          // a tile's two spectrum lines, float2
+constexpr uint32_t RG_BYTES = TD_LINES * TD_N * 4;   // its 4 x 2 filter lines [j][h], float
 constexpr uint32_t RAW_BYTES = RX_BYTES + RG_BYTES;
 constexpr uint32_t OFF_A1 = 0, OFF_B2 = OFF_A1 + A1_BYTES, OFF_TW = OFF_B2 + B2_BYTES,
                    OFF_B1 = OFF_TW + 32 * 16 * 8, OFF_A2 = OFF_B1 + 2 * B1_BYTES,
@@ -97,7 +100,31 @@ struct DftArgs {
   float scale;
   int Mh, K, s0, nlines, nimg;
   int s16;               // bfloat16 staging
+  int S, b_lo, gmax, npairs, ntiles;   // the chunk's subbands; tiling (tile_at)
 };
+
+// Tile t of a chunk: image b = b_lo + t / (gmax npairs); its subbands
+// s .. s + 3 (s = the image's first subband in the chunk + 4 f) and column
+// frequencies kx, kx + 1 (kx = 2 p).  Line l = 2 j + h of the tile is
+// (subband s + j, column frequency kx + h); nj / nh of the four subbands /
+// two column frequencies exist (nj = 0 for a tile past the image's last
+// subband: an empty tile).  The two spectrum lines serve all four filters.
+struct Tile {
+  int b, s, kx, nj, nh;
+};
+__device__ __forceinline__ Tile tile_at(const DftArgs& a, int t) {
+  Tile r;
+  const int per_img = a.gmax * a.npairs;
+  const int bi = t / per_img, rem = t - bi * per_img;
+  const int f = rem / a.npairs, p = rem - f * a.npairs;
+  r.b = a.b_lo + bi;
+  const int sa = max(a.s0, r.b * a.K), sb = min(a.s0 + a.S, (r.b + 1) * a.K);
+  r.s = sa + 4 * f;
+  r.nj = max(0, min(4, sb - r.s));
+  r.kx = 2 * p;
+  r.nh = min(2, a.Mh - r.kx);
+  return r;
+}
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -174,33 +201,29 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
       ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
 }
 
-// Warp 0: bulk copies (TMA) of the spectrum and filter lines of tile `tile`
-// into RX / RG, completing on `bar`: lane 0 arms the barrier with the byte
-// count, then lane l < 8 copies spectrum line l and lane 8 + l filter line l
-// (lines past the end are skipped).
-__device__ __forceinline__ void fetch_tile(const DftArgs& a, int tile, uint32_t rx, uint32_t rg,
+// One warp: bulk copies (TMA) of tile t's lines into RX / RG, completing on
+// `bar`.  Lane 0 arms the barrier with the byte count (zero for an empty
+// tile) and copies the two spectrum lines, one contiguous run; lane 1 + j
+// copies filter j's two lines, another.
+__device__ __forceinline__ void fetch_tile(const DftArgs& a, int t, uint32_t rx, uint32_t rg,
                                            uint32_t bar, int lane) {
-  const int l0 = tile * TD_LINES;
-  const int n = min(TD_LINES, a.nlines - l0);
+  const Tile T = tile_at(a, t);
   if (lane == 0) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    arrive_tx(bar, (uint32_t)n * TD_N * 12);
+    arrive_tx(bar, T.nj > 0 ? (uint32_t)(T.nh * TD_N * (8 + 4 * T.nj)) : 0u);
   }
   __syncwarp();
-  const int l = lane & 7;
-  if (lane < 16 && l < n) {
-    const int sl0 = l0 / a.Mh, kx0 = l0 - sl0 * a.Mh;
-    const bool wrap = kx0 + l >= a.Mh;
-    const int kx = wrap ? kx0 + l - a.Mh : kx0 + l;
-    const int s = a.s0 + sl0 + (wrap ? 1 : 0), b = s / a.K, i = s - b * a.K;
-    if (lane < 8) {
-      const bool ok = SHL_IN((size_t)b * a.Mh + kx, (size_t)a.nimg * a.Mh, CHK_TC_X);
-      // a guarded-out line reads line 0 instead (the checked build has flagged it)
-      bulk_load(rx + l * TD_N * 8, a.X + (ok ? ((size_t)b * a.Mh + kx) * TD_N : 0), TD_N * 8, bar);
-    } else {
-      const bool ok = SHL_IN((size_t)i * a.Mh + kx, (size_t)a.K * a.Mh, CHK_TC_G);
-      bulk_load(rg + l * TD_N * 4, a.G + (ok ? ((size_t)i * a.Mh + kx) * TD_N : 0), TD_N * 4, bar);
-    }
+  if (T.nj == 0) return;
+  const int i0 = T.s - T.b * a.K;
+  if (lane == 0) {
+    const bool ok = SHL_IN((size_t)T.b * a.Mh + T.kx + T.nh - 1, (size_t)a.nimg * a.Mh, CHK_TC_X);
+    // a guarded-out run reads line 0 instead (the checked build has flagged it)
+    bulk_load(rx, a.X + (ok ? ((size_t)T.b * a.Mh + T.kx) * TD_N : 0), (uint32_t)T.nh * TD_N * 8, bar);
+  } else if (lane <= T.nj) {
+    const int j = lane - 1;
+    const bool ok = SHL_IN((size_t)(i0 + j) * a.Mh + T.kx + T.nh - 1, (size_t)a.K * a.Mh, CHK_TC_G);
+    bulk_load(rg + j * 2 * TD_N * 4, a.G + (ok ? ((size_t)(i0 + j) * a.Mh + T.kx) * TD_N : 0),
+              (uint32_t)T.nh * TD_N * 4, bar);
   }
 }
 
@@ -259,7 +282,7 @@ __global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
   uint8_t* A1 = sm + OFF_A1;
   uint8_t* B2 = sm + OFF_B2;
   float2* TW = reinterpret_cast<float2*>(sm + OFF_TW);
-  const int ntiles = (a.nlines + TD_LINES - 1) / TD_LINES;
+  const int ntiles = a.ntiles;
   const int nk = (int)blockIdx.x < ntiles ? (ntiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   auto tile_of = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
   auto bar = [&](int i) { return su32(&mb[i]); };
@@ -299,8 +322,9 @@ __global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
   if (tid == 0) {
     for (int i = 0; i < NBAR; ++i) {
       const int kind = i & ~1;
-      const unsigned count = (kind == RAW_EMPTY || kind == B1_FULL || kind == D1_EMPTY ||
-                              kind == A2_FULL || kind == D2_EMPTY) ? GROUP : 1;
+      const unsigned count = (kind == RAW_EMPTY || kind == B1_FULL) ? CGROUP
+                             : (kind == D1_EMPTY || kind == A2_FULL || kind == D2_EMPTY) ? GROUP
+                                                                                           : 1;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar(i)), "r"(count) : "memory");
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -384,10 +408,12 @@ __global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
       fence_before();
       arrive(bar(D2_EMPTY + s));
+      const Tile T = tile_at(a, tile_of(k));
 #pragma unroll
       for (int mt = 0; mt < 2; ++mt) {
-        const int line = tile_of(k) * TD_LINES + 4 * mt + q;
-        if (line < a.nlines && SHL_IN(line, a.nlines, CHK_TC_OUT)) {
+        const int j = (4 * mt + q) >> 1, h = q & 1;    // tile line 4 mt + q = 2 j + h
+        const int line = (T.s + j - a.s0) * a.Mh + T.kx + h;
+        if (j < T.nj && h < T.nh && SHL_IN(line, (size_t)a.S * a.Mh, CHK_TC_OUT)) {
           if (a.s16) {
             __nv_bfloat162* o = static_cast<__nv_bfloat162*>(a.out) + (size_t)line * TD_N + lane;
 #pragma unroll
@@ -403,46 +429,52 @@ __global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
         }
       }
     }
-  } else if (warp >= W_CONV && warp < W_CONV + 4) {
-    // V[(l, n1)][(n2, c)] of the tile's 8 lines: thread (n1, g) forms
-    // n2 = 4 g .. 4 g + 3 of every line (16-byte core-matrix rows)
+  } else if (warp >= W_CONV && warp < W_CONV + 8) {
+    // V[(l, n1)][(n2, c)]: thread (n1, g, h) forms n2 = 4 g .. 4 g + 3 of the
+    // four lines l = 2 j + h of column frequency kx + h, reading its
+    // spectrum values (and 1/W) once for the four filters
     const int ct = tid - W_CONV * 32;
-    const int n1 = ct & 15, g = (ct >> 4) & 7;
+    const int n1 = ct & 15, g = (ct >> 4) & 7, h = ct >> 7;
     for (int k = 0; k < nk; ++k) {
       const int s = k & 1;
       const uint32_t ph = (k >> 1) & 1;
       if (!warp_wait(bar(RAW_FULL + s), ph, fail) || !warp_wait(bar(B1_EMPTY + s), ph ^ 1, fail))
         break;
+      const Tile T = tile_at(a, tile_of(k));
       const float2* RX = reinterpret_cast<const float2*>(sm + OFF_RAW + s * RAW_BYTES);
       const float* RG = reinterpret_cast<const float*>(sm + OFF_RAW + s * RAW_BYTES + RX_BYTES);
       uint8_t* B1 = sm + OFF_B1 + s * B1_BYTES;
-      const int l0 = tile_of(k) * TD_LINES;
-      const int sl0 = l0 / a.Mh, kx0 = l0 - sl0 * a.Mh;
-      uint4 pkd[TD_LINES];
+      const bool hv = h < T.nh;
+      // (slots of lines that do not exist hold stale data, read in bounds
+      // and replaced by zeros)
+      float2 xv[4];
+      float wv[4] = {1.f, 1.f, 1.f, 1.f};
 #pragma unroll
-      for (int l = 0; l < TD_LINES; ++l) {
+      for (int t = 0; t < 4; ++t) xv[t] = RX[h * TD_N + n1 + 16 * (4 * g + t)];
+      if (a.invW && hv) {
+#pragma unroll
+        for (int t = 0; t < 4; ++t) wv[t] = __ldg(a.invW + (size_t)(T.kx + h) * TD_N + n1 + 16 * (4 * g + t));
+      }
+      uint4 pkd[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        float gq[4];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) gq[t] = RG[(2 * j + h) * TD_N + n1 + 16 * (4 * g + t)];
         uint32_t w[4] = {0u, 0u, 0u, 0u};
-        if (l0 + l < a.nlines) {
-          const float* Wp = nullptr;
-          if (a.invW) {
-            const int kx = kx0 + l >= a.Mh ? kx0 + l - a.Mh : kx0 + l;
-            Wp = a.invW + (size_t)kx * TD_N;
-          }
+        if (j < T.nj && hv) {
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            const int ky = n1 + 16 * (4 * g + t);
-            const float2 x = RX[l * TD_N + ky];
-            float gv = RG[l * TD_N + ky] * a.scale;
-            if (Wp) gv *= __ldg(Wp + ky);
-            w[t] = pk(x.x * gv, x.y * gv);
+            const float gv = gq[t] * a.scale * wv[t];
+            w[t] = pk(xv[t].x * gv, xv[t].y * gv);
           }
         }
-        pkd[l] = make_uint4(w[0], w[1], w[2], w[3]);
+        pkd[j] = make_uint4(w[0], w[1], w[2], w[3]);
       }
       arrive(bar(RAW_EMPTY + s));                    // the line slot is read
 #pragma unroll
-      for (int l = 0; l < TD_LINES; ++l)
-        *reinterpret_cast<uint4*>(B1 + g * B1_LBO + (l * 16 + n1) * 16) = pkd[l];
+      for (int j = 0; j < 4; ++j)
+        *reinterpret_cast<uint4*>(B1 + g * B1_LBO + ((2 * j + h) * 16 + n1) * 16) = pkd[j];
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       arrive(bar(B1_FULL + s));
     }
@@ -538,7 +570,20 @@ cudaError_t launch_dec_lines_tc(int N, const float2* X, void* out, const float* 
       return e;
   }
   DftArgs a{X, out, G, invW, tw, scale, Mh, K, s0, S * Mh, nimg, s16 ? 1 : 0};
-  const int ntiles = (a.nlines + TD_LINES - 1) / TD_LINES;
+  // tiles: per image of the chunk, groups of 4 of its subbands x pairs of
+  // column frequencies (the groups start at the image's first subband)
+  a.S = S;
+  a.b_lo = s0 / K;
+  a.npairs = (Mh + 1) / 2;
+  a.gmax = 0;
+  for (int b = a.b_lo; b <= (s0 + S - 1) / K; ++b) {
+    const int sa = std::max(s0, b * K), sb = std::min(s0 + S, (b + 1) * K);
+    a.gmax = std::max(a.gmax, (sb - sa + 3) / 4);
+  }
+  const long long nt = (long long)((s0 + S - 1) / K - a.b_lo + 1) * a.gmax * a.npairs;
+  if (nt > 0x7fffffffLL) return cudaErrorInvalidValue;
+  a.ntiles = (int)nt;
+  const int ntiles = a.ntiles;
   const int grid = ntiles < nsm[dev] ? ntiles : nsm[dev];   // one CTA per SM
   k_dec_lines_tc<<<grid, TD_THREADS, TD_SMEM, st>>>(a);
   return cudaGetLastError();
