@@ -14,7 +14,8 @@
 //   stage 2  Z[k2 + 32 k1] = sum_n1 exp(2 pi i n1 k1 / 16) T[k2][n1]
 // Each stage is one real GEMM on complex data written as (re, im) pairs,
 // [re; im](out) = [[C, -S], [S, C]] [re; im](in), with the DFT matrix on one
-// side and a tile of 8 lines on the other:
+// side and a tile of 8 lines on the other (two column frequencies of four
+// subbands of one image, tile_at):
 //   stage 1  D1[2 k2 + c][(l, n1)] = sum_{(n2, c')} F32[2 k2 + c][2 n2 + c'] V[(l, n1)][2 n2 + c']
 //            (M = 128: rows 64..127 repeat rows 0..63, N = 8 lines x 16 n1 = 128, K = 64)
 //   stage 2  D2[(l, k2)][2 k1 + c] = sum_{(n1, c')} T[(l, k2)][2 n1 + c'] F16[2 k1 + c][2 n1 + c']
@@ -22,13 +23,12 @@
 // Operands sit in shared memory in the no-swizzle K-major core-matrix
 // layout [K / 8][row][8 elements] (16 bytes per row and 8-element group).
 // The work of a tile is split over warp roles that run concurrently on
-// different tiles: one warp copies a tile's spectrum and filter lines
-// (two contiguous runs, or 4 KB and 2 KB lines where the tile crosses a
-// subband) with bulk copies (TMA); eight warps form V from them; one
-// thread issues both stages' MMAs; four warps read D1 (every thread one TMEM
-// lane, a k2 and a re/im component, the other component from its neighbour
-// lane), apply the twiddle and write T; four warps read D2 and store the
-// lines.  Line slots, V, D1, T and D2 are
+// different tiles: one warp copies the tile's two spectrum lines and its
+// four filters' line pairs (contiguous runs) with bulk copies (TMA); eight
+// warps form V from them; one thread issues both stages' MMAs; four warps
+// read D1 (every thread one TMEM lane, a k2 and a re/im component, the
+// other component from its neighbour lane), apply the twiddle and write T;
+// four warps read D2 and store the lines.  Line slots, V, D1, T and D2 are
 // two-slot rings handed between the roles by mbarriers (MMA completion
 // through tcgen05.commit).  Every wait is bounded: when one runs out the
 // kernel records it (read by shl_sync), the other roles stop at their next
