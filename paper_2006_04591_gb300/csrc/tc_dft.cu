@@ -98,7 +98,7 @@ struct DftArgs {
   const float* invW;     // [Mh][512] or null
   const float2* tw;      // exp(-2 pi i q / TW_P)
   float scale;
-  int Mh, K, s0, nlines, nimg;
+  int Mh, K, s0, nimg;
   int s16;               // bfloat16 staging
   int S, b_lo, gmax, npairs, ntiles;   // the chunk's subbands; tiling (tile_at)
 };
@@ -550,7 +550,8 @@ __global__ void __launch_bounds__(TD_THREADS, 1) k_dec_lines_tc(DftArgs a) {
 
 }  // namespace
 
-// A tile's 8 lines span at most two subbands when Mh >= 8.
+// 512-point columns; planes with fewer than 8 stored column frequencies keep
+// the CUDA-core pass (the range the pass is tested on).
 bool dec_lines_tc_supported(int N, int Mh) { return N == TD_N && Mh >= TD_LINES; }
 
 cudaError_t launch_dec_lines_tc(int N, const float2* X, void* out, const float* G,
@@ -569,7 +570,7 @@ cudaError_t launch_dec_lines_tc(int N, const float2* X, void* out, const float* 
                                   (int)TD_SMEM)))
       return e;
   }
-  DftArgs a{X, out, G, invW, tw, scale, Mh, K, s0, S * Mh, nimg, s16 ? 1 : 0};
+  DftArgs a{X, out, G, invW, tw, scale, Mh, K, s0, nimg, s16 ? 1 : 0};
   // tiles: per image of the chunk, groups of 4 of its subbands x pairs of
   // column frequencies (the groups start at the image's first subband)
   a.S = S;
