@@ -53,7 +53,7 @@ namespace {
 constexpr int ROW_THREADS = 256;
 constexpr int COL_THREADS = 256;
 constexpr int MAX_LINES = 16;          // lines per CTA
-constexpr int ROW_ELEMS = 4096;        // target C * P of a row CTA (64 KB of lines)
+constexpr int ROW_ELEMS = 2048;        // target C * P of a row CTA (32 KB of lines)
 constexpr size_t COL_SMEM_CAP = 72 * 1024;   // three column CTAs per SM
 constexpr int COL_ACC = 16;            // accumulator elements per thread (C * N <= 16 * 256)
 
