@@ -54,7 +54,8 @@ constexpr int ROW_THREADS = 256;
 constexpr int COL_THREADS = 256;
 constexpr int MAX_LINES = 16;          // lines per CTA
 constexpr int ROW_ELEMS = 2048;        // target C * P of a row CTA (32 KB of lines)
-constexpr size_t COL_SMEM_CAP = 72 * 1024;   // three column CTAs per SM
+constexpr size_t COL_SMEM_CAP = 72 * 1024;   // the two line buffers of a column CTA
+constexpr int COL_LINES_MAX = 6;        // columns per CTA (4, 6, 8 measured at 480..512 rows)
 constexpr int COL_ACC = 16;            // accumulator elements per thread (C * N <= 16 * 256)
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
@@ -661,12 +662,13 @@ int row_lines(const LinePlan& pm) {
   return std::max(1, std::min(MAX_LINES, ROW_ELEMS / pm.P));
 }
 
-// Columns per CTA: at most 16, two line buffers within COL_SMEM_CAP (one
-// CTA per line when a single column needs more), and C * N <= 16 * 256 so
-// that the reconstruction's running sum fits its registers.
+// Columns per CTA: at most COL_LINES_MAX (more CTAs per SM beat longer
+// column runs), two line buffers within COL_SMEM_CAP (one CTA per line when
+// a single column needs more), and C * N <= 16 * 256 so that the
+// reconstruction's running sum fits its registers.
 int col_lines(const LinePlan& pn, int W) {
   const size_t per = 2 * (size_t)(pn.P + 1) * sizeof(float2);
-  int c = (int)std::min<size_t>(MAX_LINES, std::max<size_t>(1, COL_SMEM_CAP / per));
+  int c = (int)std::min<size_t>(COL_LINES_MAX, std::max<size_t>(1, COL_SMEM_CAP / per));
   c = std::min(c, std::max(1, COL_ACC * COL_THREADS / pn.L));
   return std::min(c, W);
 }
